@@ -1,0 +1,357 @@
+"""Benchmark of the multi-level lattice Boltzmann step on GB300.
+
+Workload (default): the two-level D2Q9 acoustic-pulse case -- coarse 512^2,
+centred fine box [128,384]^2 (513^2 fine nodes, 2 sub-steps per coarse
+step), recursive-regularized collision, tau_c = 0.5 + 1e-4, binary32
+shifted storage -- run as a batch of independent runs so that the resident
+populations (and the traffic of every step) exceed the 129 MB L2.
+
+A step is one coarse step of the whole hot path: history capture, two fine
+sub-steps with their coarse-to-fine rebuilds, the fine-to-coarse
+restriction and the coarse update, for every run of the batch.
+
+Metric: MLUPS, node updates per second counted at each level's own rate
+(sum_l 2^l N_l^active per coarse step), and the fraction of the measured HBM
+bandwidth reached by the dominant kernel (the fine-level update).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_11863_gb300 import workloads as W  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the kernel
+# sources it was taken on; ignored once the sources change.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "lattice.cuh", "ops_impl.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_11863_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, n in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def workload_case(name: str):
+    if name == "pulse2d":
+        return W.pulse_2level_d2q9("RR")
+    if name == "pulse2d_bgk":
+        return W.pulse_2level_d2q9("BGK")
+    if name == "vortex2d":
+        return W.vortex_2level_d2q9()
+    if name == "vortex3d":
+        return W.vortex_slab_d3q19()
+    if name == "pulse3d":
+        return W.pulse_3level_d3q27()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def active_counts_oracle_free(case):
+    """Active nodes per level from the layout rules (no library call)."""
+    lay = W.level_layout(case)
+    counts = []
+    for l, lv in enumerate(lay):
+        N = int(np.prod(lv["n"]))
+        if l + 1 < len(lay):
+            lo, hi = case.boxes[l]
+            ch = lay[l + 1]
+            ina = 1
+            for a in range(3):
+                ina *= (hi[a] - lo[a] - 3) if ch["boxed"][a] else lv["n"][a]
+            N -= ina
+        counts.append(N)
+    return counts
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, case, ws, rank):
+    """The oracle as it stands on the host cores: same metric and config,
+    each step a bounded sample (one coarse step of one run of the batch)."""
+    if rank != 0:
+        return
+    import oracle
+    cores = oracle.set_threads(0)
+    r = oracle.Run.from_case(case)
+    counts = active_counts_oracle_free(case)
+    U = W.updates_per_coarse_step(case, counts)
+    for _ in range(args.warmup):
+        r.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.step(1)
+    dt = time.perf_counter() - t0
+    r.close()
+    mlups = U * args.steps / dt / 1e6
+    sample = f"{args.steps} coarse steps of one {case.name} run (after {args.warmup} warm-up)"
+    line = {"impl": "reference", "metric": "MLUPS", "value": round(mlups, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case.name, "lattice": case.lattice,
+                       "collision": case.collision, "batch": 1},
+            "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(case, budget_s=15.0):
+    """Time the oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    cores = oracle.set_threads(0)
+    r = oracle.Run.from_case(case)
+    counts = active_counts_oracle_free(case)
+    U = W.updates_per_coarse_step(case, counts)
+    t0 = time.perf_counter()
+    r.step(1)
+    one = time.perf_counter() - t0
+    k = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    r.step(k)
+    dt = time.perf_counter() - t0
+    r.close()
+    return {"value": round(U * k / dt / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{k} coarse steps of one {case.name} run (FP64, OpenMP on {cores} threads)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="pulse2d")
+    ap.add_argument("--batch", type=int, default=0, help="runs per GPU (0: enough to exceed L2 4x)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_setup(args)
+    case = workload_case(args.workload)
+    if args.impl == "reference":
+        run_reference(args, case, ws, rank)
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2004_11863_gb300 import build as B
+    B.build()
+    from paper_2004_11863_gb300 import mlbm
+
+    counts = active_counts_oracle_free(case)
+    U = W.updates_per_coarse_step(case, counts)
+    s_bytes = 4 if args.storage == "fp32" else 2
+    bytes_per_run = sum(2 * case.q * s_bytes * n for n in counts)  # one update of every level
+    batch = args.batch or max(1, math.ceil(4 * L2_BYTES / (bytes_per_run / 2)))
+    stream = torch.cuda.current_stream()
+
+    # initial fields (pinned host buffers, reused by the end-to-end pass)
+    fields = []
+    for l in range(case.nlevels):
+        rho, u = W.initial_fields(case, l)
+        rp = torch.from_numpy(rho).pin_memory()
+        up = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+        fields.append((rp, up))
+
+    g = mlbm.Lbm(case.lattice, case.collision, case.tau0, case.dims, case.boxes,
+                 storage=args.storage, batch=batch, rho0=case.rho0, stream=stream.cuda_stream)
+    for l in range(case.nlevels):
+        for b in range(batch):
+            g.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    # ---------------- timed region: K graph-replayed coarse steps ----------
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    l0 = g.kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = g.kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mlups = U * batch * ws * args.steps / (ms * 1e-3) / 1e6
+    mass, mom, stable = g.diag(0)
+
+    # ---------------- per-kernel durations (CUDA events, same workload) ----
+    g.profile(True)
+    g.step(args.steps)
+    kt = {}
+    for kind, name in ((0, "update"), (1, "capture"), (2, "inject"), (3, "restrict")):
+        for l in range(case.nlevels):
+            t_ms, n = g.profile_read(kind, l)
+            if n:
+                kt[f"{name}_L{l}"] = (t_ms, n)
+    g.profile(False)
+    dom = max((k for k in kt if k.startswith("update")), key=lambda k: kt[k][0])
+    dom_level = int(dom.split("_L")[1])
+    t_ms, n = kt[dom]
+    avg_s = t_ms / n * 1e-3
+    alg_bytes = counts[dom_level] * batch * 2 * case.q * s_bytes
+    achieved = alg_bytes / avg_s / 1e9
+    peak, peak_kind = measured_peaks()
+    src_hash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get((args.workload, args.storage, dom))
+    traffic = tr["bytes_per_launch_scaled"] * batch if tr and tr["src"] == src_hash else None
+    step_total = sum(v[0] for v in kt.values()) / args.steps
+    shares = {k: round(v[0] / args.steps / step_total, 4) for k, v in kt.items()}
+
+    # ---------------- end to end through the C ABI with host buffers -------
+    torch.cuda.synchronize()
+    outs = [(torch.empty(fields[l][0].shape, dtype=torch.float64).pin_memory(),
+             torch.empty(fields[l][1].shape, dtype=torch.float64).pin_memory())
+            for l in range(case.nlevels)]
+    t0 = time.perf_counter()
+    for l in range(case.nlevels):
+        for b in range(batch):
+            g.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
+    g.step(args.steps)
+    for l in range(case.nlevels):
+        for b in range(batch):
+            rho, u = g.macros(l, b)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(4 * fields[l][0].numel() * 8 for l in range(case.nlevels)) * batch
+    d2h = h2d
+    e2e = {"value": round(U * batch * ws * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+           "note": f"lbm_init from pinned host fields, {args.steps} coarse steps, lbm_macros of "
+                   f"every level and run back to the host"}
+    g.close()
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline(case)
+    line = {
+        "metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{case.name}: {case.lattice} {case.collision} "
+                               f"{case.nlevels}-level, coarse {case.dims[0]}x{case.dims[1]}"
+                               + (f"x{case.dims[2]}" if case.dim == 3 else "")
+                               + f", tau_c={case.tau0}, {args.storage}-shifted storage",
+                   "batch_per_gpu": batch, "updates_per_coarse_step_per_run": U,
+                   "active_nodes_per_level": counts,
+                   "l2": f"inputs larger than L2: {batch} runs x {bytes_per_run / 2 / 1e6:.1f} MB "
+                         f"resident populations",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": f"k_stream_collide level {dom_level}",
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "avg_launch_ms": round(t_ms / n, 5), "src_hash": src_hash},
+        "kernel_time_share": shares,
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "stable": bool(stable),
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * mlbm.h — C ABI of the GB300 multi-level lattice Boltzmann library.
+ *
+ * The library advances the multi-level (grid-refined, ratio 2) lattice
+ * Boltzmann method of Astoul, Wissocq, Boussuge, Sengissen & Sagaut,
+ * "Analysis and reduction of spurious noise generated at grid refinement
+ * interfaces with the lattice Boltzmann method" (arXiv 2004.11863):
+ *   - per level, the fused stream-and-collide update of eq. LBMequation with
+ *     the BGK collision (eq. BGKmodel), the projected regularized collision
+ *     (eqs. reguProcedure, a1Proj, LBMscheme_reg) or the recursive
+ *     regularized collision (eqs. f1RR, a13RR), on D2Q9 (Sec. 3.1), D3Q19 or
+ *     D3Q27, with the third-order equilibrium of eq. fEqH;
+ *   - between levels, the cell-vertex transfer of Sec. 4.3: coarse-to-fine
+ *     temporal (eq. TempInt) and spatial (eq. spaceInt) interpolation with
+ *     the rescaling of eq. rescff, and fine-to-coarse filtering
+ *     (eq. filterFneq) with the rescaling of eq. rescfc; tau_f = 2 tau_c - 1/2
+ *     (eq. rescTau).
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a.  Populations are
+ * stored per level as structure-of-arrays planes of g_i = f_i - w_i rho0
+ * (FP32 or FP16), streamed in place with the AA pattern.
+ *
+ * General rules
+ *   - Every function returns 0 on success or a negative LBM_E* code; no
+ *     function throws or aborts.  lbm_strerror() names a code.
+ *   - A handle is used by one host thread at a time.  Work is issued on the
+ *     CUDA stream given to lbm_create (0 = the legacy default stream) and is
+ *     asynchronous unless a function says it synchronises.
+ *   - The handle owns all device memory it allocates (through the optional
+ *     allocator, else cudaMalloc) and frees it in lbm_destroy.  The caller
+ *     owns every host buffer it passes; host buffers are only read or written
+ *     during the call.
+ *   - Level l has node counts n[3] (lbm_level_info).  Level arrays are
+ *     ordered x fastest, then y, then z: index = (z*n[1] + y)*n[0] + x.
+ *     Level 0 is periodic on every axis.  Level l >= 1 occupies the closed
+ *     box box[l-1] given in level l-1 node units; an axis of the box that
+ *     spans the whole periodic parent axis (lo = 0, hi = parent count) is
+ *     periodic on level l with twice the parent's nodes, any other axis holds
+ *     2 (hi - lo) + 1 nodes.  Macroscopic values are in each level's own
+ *     lattice units (velocities are equal across levels, Sec. 4.1).
+ */
+#ifndef MLBM_H
+#define MLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* invalid argument or layout */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed */
+#define LBM_ECUDA (-3)     /* a CUDA runtime call or launch failed */
+#define LBM_EUNSTABLE (-4) /* non-finite mass found by lbm_diag */
+#define LBM_ESTATE (-5)    /* call out of order (e.g. step before init) */
+
+/* Lattices (Sec. 3.1; 3D sets of the same Hermite construction). */
+#define LBM_D2Q9 0
+#define LBM_D3Q19 1
+#define LBM_D3Q27 2
+/* Collisions: eq. BGKmodel; eqs. reguProcedure..LBMscheme_reg (REG);
+ * eqs. f1RR, a13RR (RR). */
+#define LBM_BGK 0
+#define LBM_REG 1
+#define LBM_RR 2
+/* Population storage: g = f - w rho0 in binary32 or binary16 (compute is
+ * always binary32). */
+#define LBM_FP32_SHIFTED 0
+#define LBM_FP16_SHIFTED 1
+
+#define LBM_MAX_LEVELS 4
+
+typedef struct lbm_ctx* lbm_handle;
+
+/* Closed box [lo, hi] of a refined level, in parent-level node units. */
+typedef struct {
+  int lo[3];
+  int hi[3];
+} lbm_box;
+
+typedef struct {
+  int lattice;   /* LBM_D2Q9 | LBM_D3Q19 | LBM_D3Q27 */
+  int collision; /* LBM_BGK | LBM_REG | LBM_RR */
+  int storage;   /* LBM_FP32_SHIFTED | LBM_FP16_SHIFTED */
+  double tau0;   /* level-0 relaxation time, > 1/2; level l uses
+                    tau_l = 2 tau_{l-1} - 1/2 (eq. rescTau) */
+  double rho0;   /* reference density of the shifted storage (usually 1) */
+  int dims[3];   /* level-0 node counts; dims[2] = 1 for D2Q9 */
+  int nlevels;   /* 1 .. LBM_MAX_LEVELS */
+  lbm_box box[LBM_MAX_LEVELS - 1];
+  int batch;     /* independent runs sharing this layout (>= 1); each run
+                    has its own populations and initial state */
+} lbm_config;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes aligned to 256 bytes,
+ * or NULL on failure; free releases a pointer alloc returned. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} lbm_allocator;
+
+/* Create a run.  Validates the layout:
+ *   - every level-l box (l >= 1) must be bounded on at least one axis;
+ *   - a bounded axis needs hi - lo >= 4; inside a periodic parent axis,
+ *     0 <= lo, hi <= parent count (the box may touch but not cross the
+ *     periodic seam) and at least 4 parent cells must stay outside; inside a
+ *     bounded parent axis, lo >= 4 and hi <= parent count - 5 (nesting
+ *     margin of four parent cells);
+ *   - tau0 > 1/2, batch >= 1, and (node count along z) x batch <= 65535
+ *     on every level.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  `alloc` may be
+ * NULL.  On success *out receives the handle; on error *out is NULL and no
+ * memory is held.  The new run must be initialised with lbm_init on every
+ * level and run before lbm_step. */
+int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
+               lbm_handle* out);
+
+/* Level geometry: node counts n[3], relaxation time tau_l, and the number of
+ * active nodes (nodes that are updated; the parent nodes strictly inside a
+ * child's restriction ring are inactive).  Any output pointer may be NULL. */
+int lbm_level_info(lbm_handle h, int level, int* n, double* tau,
+                   long long* n_active);
+
+/* Set every node of one level of one run to the equilibrium f^(0)(rho, u)
+ * (eq. fEqH; initial populations carry no off-equilibrium part).
+ * rho: host [N] doubles; u: host [3][N] doubles (u[2] ignored in 2D).
+ * Synchronises on the handle's stream. */
+int lbm_init(lbm_handle h, int level, int run, const double* rho,
+             const double* u);
+
+/* Advance every run by n_coarse level-0 steps (level l takes 2^l sub-steps
+ * each, Sec. 4.3).  Asynchronous.  The first step after lbm_init starts the
+ * coarse-to-fine temporal interpolation with the linear rule; later steps
+ * use eq. TempInt.  Steps after the first replay captured CUDA graphs unless
+ * graphs were switched off with lbm_set_graphs. */
+int lbm_step(lbm_handle h, int n_coarse);
+
+/* Use (1, default) or bypass (0) CUDA graphs in lbm_step. */
+int lbm_set_graphs(lbm_handle h, int enable);
+
+/* Macroscopic density and velocity of one level of one run, from the
+ * post-collision state after the last step: rho host [N], u host [3][N]
+ * (u[2] = 0 in 2D); NaN at inactive nodes.  Synchronises. */
+int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u);
+
+/* Same as lbm_macros but into device buffers (float): rho_dev [N],
+ * u_dev [3][N].  Asynchronous on the handle's stream. */
+int lbm_macros_device(lbm_handle h, int level, int run, float* rho_dev,
+                      float* u_dev);
+
+/* Post-collision shifted populations g_i = f_i - w_i rho0 of one level of
+ * one run, host [q][N] doubles, in the library's velocity order (returned
+ * by lbm_lattice).  Synchronises. */
+int lbm_populations(lbm_handle h, int level, int run, double* g);
+
+/* The library's velocity set: xi host [q][3] ints, w host [q] doubles.
+ * Returns q (> 0) or a negative code. */
+int lbm_lattice(int lattice, int* xi, double* w);
+
+/* Register probe nodes: n nodes of `level`, ijk host [n][3] node indices.
+ * After every coarse step the density and velocity of each probe of each
+ * run are recorded on the device (capacity: 65536 coarse steps; older
+ * samples are overwritten).  Replaces any earlier probe set. */
+int lbm_probe_add(lbm_handle h, int level, int n, const int* ijk);
+
+/* Drain the probe record: out host [n_steps][batch][n][4] doubles
+ * (rho, u_x, u_y, u_z), oldest first, at most max_steps; *n_steps receives
+ * the number of recorded steps returned.  Synchronises. */
+int lbm_probe(lbm_handle h, double* out, int max_steps, int* n_steps);
+
+/* FP64 conservation diagnostics of one run, reduced on the device in a fixed
+ * order (deterministic): per level, mass[l] = sum over active nodes of
+ * (rho - rho0) and mom[l][3] = sum of rho u, in level lattice units.
+ * Returns LBM_EUNSTABLE if any sum is not finite.  Synchronises. */
+int lbm_diag(lbm_handle h, int run, double* mass, double* mom);
+
+/* Block until all work issued by the handle has finished. */
+int lbm_sync(lbm_handle h);
+
+/* Count of CUDA kernel launches issued by this handle so far (graph
+ * replays count every kernel node they contain). */
+long long lbm_kernel_launches(lbm_handle h);
+
+/* Per-kernel timing.  lbm_profile(h, 1) clears the record and makes the
+ * following lbm_step calls launch eagerly (no graph replay) with a CUDA
+ * event pair around every kernel on the handle's stream; lbm_profile(h, 0)
+ * stops recording.  Both synchronise. */
+int lbm_profile(lbm_handle h, int enable);
+
+/* Sum of the recorded kernel durations (ms) and their count for one kernel
+ * kind (0 level update, 1 history capture, 2 coarse-to-fine rebuild,
+ * 3 fine-to-coarse restriction, 4 probe sampling) on one level (-1: all
+ * levels; the level is the one updated, or the parent for 1 and 3).
+ * Synchronises. */
+int lbm_profile_read(lbm_handle h, int kind, int level, double* total_ms,
+                     long long* count);
+
+/* Release the handle and all device memory it owns. NULL is ignored. */
+void lbm_destroy(lbm_handle h);
+
+/* Static description of a return code. */
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLBM_H */

@@ -1,0 +1,81 @@
+// Plain descriptors passed by value from the host scheduler to the kernels.
+// They describe where a level's populations live and which nodes take part
+// in each interface operation of the cell-vertex coupling (Sec. 4.3).
+#pragma once
+#include <cstdint>
+
+namespace mlbm {
+
+// One level's population storage: `batch` runs, each a set of q planes of
+// `plane` elements (structure of arrays), x fastest.  Node (x, y, z) sits at
+// element off + (z * SY + y) * SX + x of a plane.  Bounded axes carry a
+// one-node ghost skin (x = -1 and x = n[0] on bounded x; y and z likewise);
+// periodic axes wrap.  Rows are padded to a multiple of 32 elements so that
+// node x = 0 of every row is 128-byte aligned for binary32 storage.
+struct LevelView {
+  void* f;
+  long long plane;
+  long long run_stride;  // q * plane
+  long long off;
+  int n[3];
+  int per[3];
+  int SX, SY;
+  int batch;
+  // Parent nodes strictly inside the child's restriction ring are not
+  // updated (inactive); empty when the level has no child.
+  int has_ina;
+  int ina_lo[3], ina_hi[3];
+};
+
+constexpr int kMaxFaces = 6;
+
+// Threads per block of the FP64 diagnostic reduction.
+constexpr int kDiagThreads = 256;
+
+// Parent-level history of (drho, u_x, u_y, u_z, f1_0 .. f1_{q-1}) on the
+// surface of a child box, extended by one parent cell past its edges, in
+// three time slots (t-1, t, t+1).  Face f (axis[f], side[f]) has ext[f][a]
+// entries along axis a; local index i_a maps to parent coordinate
+// base[f][a] + i_a (wrapped on periodic parent axes).
+// Layout: hist[((run * 3 + slot) * nv + v) * K + k].
+struct RingDesc {
+  float* hist;
+  long long K;
+  int nv;
+  int nf;
+  int axis[kMaxFaces], side[kMaxFaces];
+  long long start[kMaxFaces + 1];
+  int ext[kMaxFaces][3];
+  int base[kMaxFaces][3];
+  int pn[3];      // parent node counts
+  int pper[3];    // parent periodic axes
+  int boxed[3];   // child axes bounded by the box
+};
+
+// Child-level c->f boundary nodes (TF and IE, the outer node layer of the
+// child box), one entry per node: face f holds the nodes with x[axis] = 0
+// (side 0) or n-1 (side 1) that lie on no earlier face; along axis a the
+// face covers child coordinates lo[f][a] .. lo[f][a] + ext[f][a] - 1.
+struct BndDesc {
+  long long count;
+  int nf;
+  int axis[kMaxFaces], side[kMaxFaces];
+  long long start[kMaxFaces + 1];
+  int lo[kMaxFaces][3], ext[kMaxFaces][3];
+};
+
+// Parent-level f->c nodes (TN, the parent nodes one parent cell inside the
+// child box), one entry per node.  Face f covers box-relative coordinates
+// rlo[f][a] .. rlo[f][a] + rext[f][a] - 1 along each axis (absolute parent
+// coordinates on axes the box spans).
+struct TnDesc {
+  long long count;
+  int nf;
+  int axis[kMaxFaces], side[kMaxFaces];
+  long long start[kMaxFaces + 1];
+  int rlo[kMaxFaces][3], rext[kMaxFaces][3];
+  int lo[3];      // child box lo (parent units)
+  int boxed[3];
+};
+
+}  // namespace mlbm

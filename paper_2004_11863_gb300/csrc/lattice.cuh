@@ -1,0 +1,269 @@
+// Velocity sets and the Hermite-equilibrium / collision arithmetic of the
+// level update, evaluated in binary32 on shifted populations
+// g_i = f_i - w_i rho0.
+//
+// Lattices: D2Q9 in the velocity order of Sec. 3.1 (eqs. xi_i, w_i); D3Q19
+// and D3Q27 built the same way (weights 1/3, 1/18, 1/36 and 8/27, 2/27, 1/54,
+// 1/216).  c_s^2 = 1/3 on all three.
+//
+// Equilibrium (eq. fEqH truncated at third order, eq. fEqO3 in 2D):
+//   f0_i = w_i rho [1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u + T3_i(u u u)],
+// where T3 is the lattice-supported third-order Hermite term set:
+//   D2Q9:  H_xxy, H_xyy with 1/(2 cs^6);
+//   D3Q27: the six H_aab with 1/(2 cs^6) and H_xyz with 1/cs^6;
+//   D3Q19: for each odd axis b the orthogonal pair H_aab +- H_ccb, with
+//          1/(2 cs^6) on the sum and 1/(6 cs^6) on the difference
+//          (H_aab and H_ccb are not orthogonal on D3Q19 and H_xyz vanishes).
+// Regularized collisions (eqs. reguProcedure, a1Proj, LBMscheme_reg, f1RR,
+// a13RR): a1 = sum H2 (f - f0) is formed directly from the shifted second
+// moment, a1_ab = sum xi_a xi_b g - rho u_a u_b - drho cs^2 delta_ab, and the
+// post-collision state is f0 + (1 - 1/tau) f1 with
+//   f1_i = w_i [4.5 H2_i : a1 + T3_i(a1^(3))],
+//   a1^(3)_abc = u_a a1_bc + u_b a1_ac + u_c a1_ab   (RR; zero for REG).
+#pragma once
+#include <cuda_fp16.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace mlbm {
+
+// ---------------------------------------------------------------- unrolling
+template <class F, int... I>
+__host__ __device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+  sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ------------------------------------------------------------------ lattices
+struct D2Q9 {
+  static constexpr int Q = 9, D = 2, ID = 0;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[9][3] = {{0, 0, 0},  {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0},
+                             {1, 1, 0},  {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+// 3D sets: rest, then the 6 axis neighbours, then the 12 edge neighbours,
+// then (D3Q27) the 8 corners; opposite pairs are adjacent (i, i+1) after 0.
+struct D3Q19 {
+  static constexpr int Q = 19, D = 3, ID = 1;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                              {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                              {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                              {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+struct D3Q27 {
+  static constexpr int Q = 27, D = 3, ID = 2;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    constexpr int t[27][3] = {
+        {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+        {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+        {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},  {1, 1, 1},  {-1, -1, -1},
+        {1, 1, -1},  {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 8.0 / 27.0 : (i < 7 ? 2.0 / 27.0 : (i < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+  }
+};
+
+template <class L>
+__host__ __device__ constexpr int opp(int i) {
+  int k = 0;
+  for (int j = 0; j < L::Q; ++j)
+    if (L::c(j, 0) == -L::c(i, 0) && L::c(j, 1) == -L::c(i, 1) && L::c(j, 2) == -L::c(i, 2)) k = j;
+  return k;
+}
+
+// Third-order Hermite polynomial H_aab(xi_i) = xi_a^2 xi_b - cs^2 xi_b.
+template <class L>
+__host__ __device__ constexpr double h3(int i, int a, int b) {
+  return double(L::c(i, a) * L::c(i, a) * L::c(i, b)) - double(L::c(i, b)) / 3.0;
+}
+
+// Third-order coefficient set, indexed [xxy, xxz, yyx, yyz, zzx, zzy, xyz].
+enum { XXY = 0, XXZ, YYX, YYZ, ZZX, ZZY, XYZ };
+
+// T3_i(A): the lattice-supported third-order term of the Hermite expansion
+// for coefficients A (already including every factor except w_i).
+template <class L, int I, class T>
+__host__ __device__ __forceinline__ T third(const T (&A)[7]) {
+  if constexpr (L::ID == 0) {
+    constexpr T hxxy = T(13.5 * h3<L>(I, 0, 1)), hyyx = T(13.5 * h3<L>(I, 1, 0));
+    return hxxy * A[XXY] + hyyx * A[YYX];
+  } else if constexpr (L::ID == 2) {
+    constexpr T k0 = T(13.5 * h3<L>(I, 0, 1)), k1 = T(13.5 * h3<L>(I, 0, 2)),
+                k2 = T(13.5 * h3<L>(I, 1, 0)), k3 = T(13.5 * h3<L>(I, 1, 2)),
+                k4 = T(13.5 * h3<L>(I, 2, 0)), k5 = T(13.5 * h3<L>(I, 2, 1)),
+                k6 = T(27.0 * L::c(I, 0) * L::c(I, 1) * L::c(I, 2));
+    return k0 * A[XXY] + k1 * A[XXZ] + k2 * A[YYX] + k3 * A[YYZ] + k4 * A[ZZX] + k5 * A[ZZY] +
+           k6 * A[XYZ];
+  } else {
+    // odd axis y: (xxy, zzy); odd axis x: (yyx, zzx); odd axis z: (xxz, yyz)
+    constexpr T py = T(13.5 * (h3<L>(I, 0, 1) + h3<L>(I, 2, 1))),
+                my = T(4.5 * (h3<L>(I, 0, 1) - h3<L>(I, 2, 1)));
+    constexpr T px = T(13.5 * (h3<L>(I, 1, 0) + h3<L>(I, 2, 0))),
+                mx = T(4.5 * (h3<L>(I, 1, 0) - h3<L>(I, 2, 0)));
+    constexpr T pz = T(13.5 * (h3<L>(I, 0, 2) + h3<L>(I, 1, 2))),
+                mz = T(4.5 * (h3<L>(I, 0, 2) - h3<L>(I, 1, 2)));
+    return py * (A[XXY] + A[ZZY]) + my * (A[XXY] - A[ZZY]) + px * (A[YYX] + A[ZZX]) +
+           mx * (A[YYX] - A[ZZX]) + pz * (A[XXZ] + A[YYZ]) + mz * (A[XXZ] - A[YYZ]);
+  }
+}
+
+// xi_i . v with compile-time components.
+template <class L, int I, class T>
+__host__ __device__ __forceinline__ T cdot(T vx, T vy, T vz) {
+  T s = T(0);
+  if constexpr (L::c(I, 0) == 1) s += vx;
+  if constexpr (L::c(I, 0) == -1) s -= vx;
+  if constexpr (L::c(I, 1) == 1) s += vy;
+  if constexpr (L::c(I, 1) == -1) s -= vy;
+  if constexpr (L::D == 3) {
+    if constexpr (L::c(I, 2) == 1) s += vz;
+    if constexpr (L::c(I, 2) == -1) s -= vz;
+  }
+  return s;
+}
+
+// Macroscopic moments of shifted populations: drho = sum g, j = sum xi g.
+template <class L, class T>
+__host__ __device__ __forceinline__ void moments(const T (&g)[L::Q], T& drho, T& jx, T& jy,
+                                                 T& jz) {
+  drho = jx = jy = jz = T(0);
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    drho += g[i];
+    if constexpr (L::c(i, 0) == 1) jx += g[i];
+    if constexpr (L::c(i, 0) == -1) jx -= g[i];
+    if constexpr (L::c(i, 1) == 1) jy += g[i];
+    if constexpr (L::c(i, 1) == -1) jy -= g[i];
+    if constexpr (L::c(i, 2) == 1) jz += g[i];
+    if constexpr (L::c(i, 2) == -1) jz -= g[i];
+  });
+}
+
+// Shifted equilibrium g0_i = f0_i(rho0 + drho, u) - w_i rho0.
+template <class L, class T>
+__host__ __device__ __forceinline__ void equilibrium(T drho, T rho, T ux, T uy, T uz,
+                                                     T (&g0)[L::Q]) {
+  if constexpr (L::D == 2) uz = T(0);
+  T A[7];
+  A[XXY] = ux * ux * uy;
+  A[XXZ] = ux * ux * uz;
+  A[YYX] = uy * uy * ux;
+  A[YYZ] = uy * uy * uz;
+  A[ZZX] = uz * uz * ux;
+  A[ZZY] = uz * uz * uy;
+  A[XYZ] = ux * uy * uz;
+  const T usq = T(1.5) * (ux * ux + uy * uy + uz * uz);
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const T cu = cdot<L, i>(ux, uy, uz);
+    const T e = T(3) * cu + T(4.5) * cu * cu - usq + third<L, i>(A);
+    g0[i] = T(L::w(i)) * (drho + rho * e);
+  });
+}
+
+// In-place collision of shifted populations g -> post-collision state.
+// COLL: 0 BGK (eq. BGKmodel), 1 REG (eq. LBMscheme_reg with H^(2) only),
+// 2 RR (eqs. f1RR, a13RR).  omega = 1 - 1/tau.
+template <class L, int COLL>
+__device__ __forceinline__ void collide(float (&g)[L::Q], float omega, float rho0) {
+  float drho, jx, jy, jz;
+  moments<L>(g, drho, jx, jy, jz);
+  const float rho = rho0 + drho;
+  const float inv = 1.0f / rho;
+  const float ux = jx * inv, uy = jy * inv, uz = (L::D == 3) ? jz * inv : 0.0f;
+  float g0[L::Q];
+  equilibrium<L>(drho, rho, ux, uy, uz, g0);
+  if constexpr (COLL == 0) {
+    sfor<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      g[i] = g0[i] + omega * (g[i] - g0[i]);
+    });
+  } else {
+    // shifted second moments
+    float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+    sfor<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+      if constexpr (cx != 0) pxx += g[i];
+      if constexpr (cy != 0) pyy += g[i];
+      if constexpr (cz != 0) pzz += g[i];
+      if constexpr (cx * cy == 1) pxy += g[i];
+      if constexpr (cx * cy == -1) pxy -= g[i];
+      if constexpr (cx * cz == 1) pxz += g[i];
+      if constexpr (cx * cz == -1) pxz -= g[i];
+      if constexpr (cy * cz == 1) pyz += g[i];
+      if constexpr (cy * cz == -1) pyz -= g[i];
+    });
+    const float dc = drho * (1.0f / 3.0f);
+    const float axx = pxx - rho * ux * ux - dc;
+    const float ayy = pyy - rho * uy * uy - dc;
+    const float azz = (L::D == 3) ? pzz - rho * uz * uz - dc : 0.0f;
+    const float axy = pxy - rho * ux * uy;
+    const float axz = (L::D == 3) ? pxz - rho * ux * uz : 0.0f;
+    const float ayz = (L::D == 3) ? pyz - rho * uy * uz : 0.0f;
+    float A[7] = {0, 0, 0, 0, 0, 0, 0};
+    if constexpr (COLL == 2) {
+      A[XXY] = 2.0f * ux * axy + uy * axx;
+      A[YYX] = 2.0f * uy * axy + ux * ayy;
+      if constexpr (L::D == 3) {
+        A[XXZ] = 2.0f * ux * axz + uz * axx;
+        A[YYZ] = 2.0f * uy * ayz + uz * ayy;
+        A[ZZX] = 2.0f * uz * axz + ux * azz;
+        A[ZZY] = 2.0f * uz * ayz + uy * azz;
+        A[XYZ] = ux * ayz + uy * axz + uz * axy;
+      }
+    }
+    sfor<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+      // 4.5 * H2_i : a1, with H2_aa = xi_a^2 - 1/3 and both off-diagonal terms
+      constexpr float dxx = 4.5f * (float(cx * cx) - 1.0f / 3.0f);
+      constexpr float dyy = 4.5f * (float(cy * cy) - 1.0f / 3.0f);
+      constexpr float oxy = 9.0f * float(cx * cy);
+      float h2a = dxx * axx + dyy * ayy + oxy * axy;
+      if constexpr (L::D == 3) {
+        constexpr float dzz = 4.5f * (float(cz * cz) - 1.0f / 3.0f);
+        constexpr float oxz = 9.0f * float(cx * cz), oyz = 9.0f * float(cy * cz);
+        h2a += dzz * azz + oxz * axz + oyz * ayz;
+      }
+      float f1 = h2a;
+      if constexpr (COLL == 2) f1 += third<L, i>(A);
+      g[i] = g0[i] + omega * (float(L::w(i)) * f1);
+    });
+  }
+}
+
+// ------------------------------------------------------------ storage types
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+  __device__ __forceinline__ static float ld(const float* p) { return *p; }
+  __device__ __forceinline__ static void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+  __device__ __forceinline__ static float ld(const __half* p) { return __half2float(*p); }
+  __device__ __forceinline__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+}  // namespace mlbm

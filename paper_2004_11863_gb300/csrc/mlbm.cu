@@ -1,0 +1,831 @@
+// Host side of the library: level layout, interface descriptors, the
+// recursive level schedule of Sec. 4.3, CUDA-graph capture of a coarse step
+// and the C ABI declared in include/mlbm.h.
+//
+// Schedule of one step of level l (parent of level l+1), issued as kernels:
+//   [l >= 1] K3 inject level l's TF/IE nodes from its parent's history;
+//   [child]  K2 record level l's pre-collision state at t+1 on the child box
+//            surface (steps 2a/2b/2g need it before the fine sub-steps);
+//            advance(l+1) with the temporal weights of eq. TempInt (t+1/2);
+//            K4 restrict the child's pre-collision state at its t+1 into
+//            level l's TN nodes (step 3d) -- it only needs the child's state
+//            after its first sub-step, which already determines it;
+//            advance(l+1) with the direct transfer (t+1);
+//   K1 stream + collide level l (steps 2a + 3e for the coarse level).
+// The coarse level therefore streams and collides in one fused pass after
+// the fine sub-steps, as step 2a / step 3e allow: nothing it streams is
+// changed by the fine sub-steps except its TN nodes, which step 3d rebuilds.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/mlbm.h"
+#include "desc.h"
+#include "lattice.cuh"
+#include "ops.cuh"
+
+using namespace mlbm;
+
+namespace {
+
+thread_local char g_errmsg[256] = "";
+
+#define CK(expr)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      snprintf(g_errmsg, sizeof(g_errmsg), "%s: %s (%s:%d)", #expr,                 \
+               cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+      return LBM_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+struct Level {
+  int n[3] = {1, 1, 1};
+  int per[3] = {1, 1, 1};
+  int boxed[3] = {0, 0, 0};
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // box in parent units (l >= 1)
+  double tau = 1.0;
+  LevelView view{};
+  void* mem = nullptr;
+  size_t bytes = 0;
+  int last = 0;  // parity of the last update (0 after init)
+  long long nsteps = 0;
+  long long n_nodes = 0, n_active = 0;
+  // interface with the parent (l >= 1)
+  RingDesc ring{};
+  BndDesc bnd{};
+  TnDesc tn{};  // TN nodes of the parent
+  void* hist_mem = nullptr;
+};
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_config cfg{};
+  int q = 0, D = 0, nlev = 0, batch = 1;
+  Ops ops{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cur = nullptr;
+  bool has_alloc = false;
+  lbm_allocator alloc{};
+  Level lev[LBM_MAX_LEVELS];
+  std::vector<char> inited;  // [level][run]
+  bool ready = false;
+  bool seeded = false;
+  long long coarse_steps = 0;
+  bool use_graphs = true;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  long long exec_nodes[2] = {0, 0};
+  long long launches = 0;
+  // per-kernel CUDA-event timing (lbm_profile)
+  struct Rec {
+    int kind, level;
+    cudaEvent_t a, b;
+  };
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
+  size_t pool_used = 0;
+  cudaEvent_t next_event() {
+    if (pool_used == event_pool.size()) {
+      cudaEvent_t e = nullptr;
+      cudaEventCreate(&e);
+      event_pool.push_back(e);
+    }
+    return event_pool[pool_used++];
+  }
+  // probes
+  int probe_level = -1, probe_n = 0, probe_cap = 0;
+  int* probe_ijk = nullptr;
+  double* probe_rec = nullptr;
+  unsigned long long* probe_counter = nullptr;
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (has_alloc) return alloc.alloc(bytes, alloc.user);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    if (has_alloc)
+      alloc.free(p, alloc.user);
+    else
+      cudaFree(p);
+  }
+};
+
+namespace {
+
+Ops ops_for(int lattice) {
+  switch (lattice) {
+    case LBM_D2Q9: return make_ops<D2Q9>();
+    case LBM_D3Q19: return make_ops<D3Q19>();
+    default: return make_ops<D3Q27>();
+  }
+}
+
+void drop_graphs(lbm_ctx* h) {
+  for (int k = 0; k < 2; ++k)
+    if (h->exec[k]) {
+      cudaGraphExecDestroy(h->exec[k]);
+      h->exec[k] = nullptr;
+      h->exec_nodes[k] = 0;
+    }
+}
+
+void release(lbm_ctx* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  for (int l = 0; l < h->nlev; ++l) {
+    h->dfree(h->lev[l].mem);
+    h->dfree(h->lev[l].hist_mem);
+    h->lev[l].mem = h->lev[l].hist_mem = nullptr;
+  }
+  h->dfree(h->probe_ijk);
+  h->dfree(h->probe_rec);
+  h->dfree(h->probe_counter);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  h->event_pool.clear();
+}
+
+// Node counts and axis kinds of every level; checks the layout rules.
+int build_layout(lbm_ctx* h) {
+  const lbm_config& c = h->cfg;
+  const int D = h->D;
+  Level& L0 = h->lev[0];
+  for (int a = 0; a < 3; ++a) {
+    L0.n[a] = a < D ? c.dims[a] : 1;
+    L0.per[a] = 1;
+    L0.boxed[a] = 0;
+    if (L0.n[a] < 1) return LBM_EINVAL;
+  }
+  if (D == 2 && c.dims[2] != 1) return LBM_EINVAL;
+  for (int a = 0; a < D; ++a)
+    if (L0.n[a] < 4) return LBM_EINVAL;
+  L0.tau = c.tau0;
+  for (int l = 1; l < h->nlev; ++l) {
+    Level& p = h->lev[l - 1];
+    Level& v = h->lev[l];
+    int any = 0;
+    for (int a = 0; a < 3; ++a) {
+      v.lo[a] = c.box[l - 1].lo[a];
+      v.hi[a] = c.box[l - 1].hi[a];
+      if (a >= D) {
+        v.n[a] = 1;
+        v.per[a] = 1;
+        v.boxed[a] = 0;
+        continue;
+      }
+      const int E = v.hi[a] - v.lo[a];
+      if (p.per[a] && v.lo[a] == 0 && E == p.n[a]) {
+        v.boxed[a] = 0;
+        v.per[a] = 1;
+        v.n[a] = 2 * p.n[a];
+      } else {
+        if (E < 4) return LBM_EINVAL;
+        if (p.per[a]) {
+          if (v.lo[a] < 0 || v.hi[a] > p.n[a] || p.n[a] - E < 4) return LBM_EINVAL;
+        } else {
+          if (v.lo[a] < 4 || v.hi[a] > p.n[a] - 5) return LBM_EINVAL;
+        }
+        v.boxed[a] = 1;
+        v.per[a] = 0;
+        v.n[a] = 2 * E + 1;
+        any = 1;
+      }
+    }
+    if (!any) return LBM_EINVAL;
+    v.tau = 2.0 * p.tau - 0.5;  // eq. rescTau
+  }
+  return LBM_OK;
+}
+
+// Storage geometry (ghost skin on bounded axes, 32-element row pitch).
+void build_view(lbm_ctx* h, int l) {
+  Level& v = h->lev[l];
+  LevelView& w = v.view;
+  int g[3];
+  for (int a = 0; a < 3; ++a) g[a] = v.per[a] ? 0 : 1;
+  w.SX = round_up(v.n[0] + 2 * g[0], 32);
+  w.SY = v.n[1] + 2 * g[1];
+  const long long SZ = v.n[2] + 2 * g[2];
+  w.off = 32 + ((long long)g[2] * w.SY + g[1]) * w.SX;
+  long long need = w.off + SZ * w.SY * (long long)w.SX + 32;
+  w.plane = (need + 63) / 64 * 64;
+  w.run_stride = w.plane * h->q;
+  for (int a = 0; a < 3; ++a) {
+    w.n[a] = v.n[a];
+    w.per[a] = v.per[a];
+  }
+  w.batch = h->batch;
+  w.has_ina = 0;
+  v.n_nodes = (long long)v.n[0] * v.n[1] * v.n[2];
+  v.n_active = v.n_nodes;
+  if (l + 1 < h->nlev) {
+    const Level& c = h->lev[l + 1];
+    w.has_ina = 1;
+    long long ina = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (c.boxed[a]) {
+        w.ina_lo[a] = c.lo[a] + 2;
+        w.ina_hi[a] = c.hi[a] - 2;
+      } else {
+        w.ina_lo[a] = 0;
+        w.ina_hi[a] = v.n[a] - 1;
+      }
+      ina *= (w.ina_hi[a] - w.ina_lo[a] + 1);
+    }
+    v.n_active = v.n_nodes - ina;
+  }
+  v.bytes = (size_t)w.run_stride * h->batch *
+            (h->cfg.storage == LBM_FP16_SHIFTED ? 2 : 4);
+}
+
+// Interface descriptors of level l (l >= 1) against its parent.
+void build_interface(lbm_ctx* h, int l) {
+  Level& c = h->lev[l];
+  const Level& p = h->lev[l - 1];
+  const int D = h->D;
+  RingDesc& R = c.ring;
+  BndDesc& B = c.bnd;
+  TnDesc& T = c.tn;
+  R.nf = B.nf = T.nf = 0;
+  R.start[0] = B.start[0] = T.start[0] = 0;
+  for (int a = 0; a < 3; ++a) {
+    R.pn[a] = p.n[a];
+    R.pper[a] = p.per[a];
+    R.boxed[a] = c.boxed[a];
+    T.lo[a] = c.lo[a];
+    T.boxed[a] = c.boxed[a];
+  }
+  for (int a = 0; a < D; ++a) {
+    if (!c.boxed[a]) continue;
+    for (int side = 0; side < 2; ++side) {
+      int f = R.nf;
+      R.axis[f] = B.axis[f] = T.axis[f] = a;
+      R.side[f] = B.side[f] = T.side[f] = side;
+      long long rs = 1, bs = 1, ts = 1;
+      for (int b = 0; b < 3; ++b) {
+        const int E = c.hi[b] - c.lo[b];
+        // history ring (parent nodes), extended one parent cell past edges
+        if (b == a) {
+          R.ext[f][b] = 1;
+          R.base[f][b] = side ? c.hi[b] : c.lo[b];
+        } else if (b >= D) {
+          R.ext[f][b] = 1;
+          R.base[f][b] = 0;
+        } else if (c.boxed[b]) {
+          R.ext[f][b] = E + 3;
+          R.base[f][b] = c.lo[b] - 1;
+        } else {
+          R.ext[f][b] = p.n[b];
+          R.base[f][b] = 0;
+        }
+        // child boundary nodes, each on its first face only
+        if (b == a) {
+          B.lo[f][b] = side ? c.n[b] - 1 : 0;
+          B.ext[f][b] = 1;
+        } else if (b >= D || !c.boxed[b]) {
+          B.lo[f][b] = 0;
+          B.ext[f][b] = c.n[b];
+        } else if (b < a) {
+          B.lo[f][b] = 1;
+          B.ext[f][b] = c.n[b] - 2;
+        } else {
+          B.lo[f][b] = 0;
+          B.ext[f][b] = c.n[b];
+        }
+        // parent TN nodes (box-relative on bounded axes), first face only
+        if (b == a) {
+          T.rlo[f][b] = side ? E - 1 : 1;
+          T.rext[f][b] = 1;
+        } else if (b >= D) {
+          T.rlo[f][b] = 0;
+          T.rext[f][b] = 1;
+        } else if (!c.boxed[b]) {
+          T.rlo[f][b] = 0;
+          T.rext[f][b] = p.n[b];
+        } else if (b < a) {
+          T.rlo[f][b] = 2;
+          T.rext[f][b] = E - 3;
+        } else {
+          T.rlo[f][b] = 1;
+          T.rext[f][b] = E - 1;
+        }
+        rs *= R.ext[f][b];
+        bs *= B.ext[f][b];
+        ts *= T.rext[f][b];
+      }
+      R.start[f + 1] = R.start[f] + rs;
+      B.start[f + 1] = B.start[f] + bs;
+      T.start[f + 1] = T.start[f] + ts;
+      R.nf = B.nf = T.nf = f + 1;
+    }
+  }
+  R.K = R.start[R.nf];
+  R.nv = 4 + h->q;
+  B.count = B.start[B.nf];
+  T.count = T.start[T.nf];
+}
+
+const float kTimeQuad[3] = {-1.0f / 8.0f, 3.0f / 4.0f, 3.0f / 8.0f};  // eq. TempInt
+const float kTimeLin[3] = {0.0f, 0.5f, 0.5f};   // first step: no t-1 yet
+const float kTimeDirect[3] = {0.0f, 0.0f, 1.0f};  // synchronous sub-step
+
+inline float omega_of(double tau) { return (float)(1.0 - 1.0 / tau); }
+
+// Issue one kernel (when `launch`), bracketed by timing events when the
+// handle is profiling (kind: 0 level update, 1 capture, 2 inject,
+// 3 restrict, 4 probe).
+#define LAUNCH_K(kind_, level_, expr)                                    \
+  do {                                                                   \
+    if (launch) {                                                        \
+      cudaEvent_t ea_ = nullptr, eb_ = nullptr;                          \
+      if (h->profiling) {                                                \
+        ea_ = h->next_event();                                           \
+        eb_ = h->next_event();                                           \
+        CK(cudaEventRecord(ea_, h->cur));                                \
+      }                                                                  \
+      CK(expr);                                                          \
+      ++h->launches;                                                     \
+      if (h->profiling) {                                                \
+        CK(cudaEventRecord(eb_, h->cur));                                \
+        h->recs.push_back({kind_, level_, ea_, eb_});                    \
+      }                                                                  \
+    }                                                                    \
+  } while (0)
+#define LAUNCH(expr) LAUNCH_K(-1, -1, expr)
+
+// One step of level l with its finer levels (see the file comment).
+int advance(lbm_ctx* h, int l, const float* wt, bool launch) {
+  Level& v = h->lev[l];
+  const int st = h->cfg.storage;
+  const float rho0 = (float)h->cfg.rho0;
+  const int par = 1 - v.last;
+  if (l >= 1) {
+    const Level& p = h->lev[l - 1];
+    const float resc = (float)(v.tau / (2.0 * p.tau));  // eq. rescff
+    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, resc, par, rho0, h->cur));
+  }
+  if (l + 1 < h->nlev) {
+    Level& c = h->lev[l + 1];
+    LAUNCH_K(1, l, h->ops.capture(v.view, c.ring, st, par, 0, rho0, h->cur));
+    int rc = advance(h, l + 1, v.nsteps == 0 ? kTimeLin : kTimeQuad, launch);
+    if (rc) return rc;
+    const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
+    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, rho0, h->cur));
+    rc = advance(h, l + 1, kTimeDirect, launch);
+    if (rc) return rc;
+  }
+  LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), rho0, h->cur));
+  v.last = par;
+  v.nsteps++;
+  return LBM_OK;
+}
+
+int probe_launch(lbm_ctx* h, bool launch) {
+  if (h->probe_n <= 0) return LBM_OK;
+  const Level& v = h->lev[h->probe_level];
+  LAUNCH_K(4, h->probe_level, h->ops.probe(v.view, h->cfg.storage, v.last, h->probe_ijk, h->probe_n, h->probe_rec,
+                      h->probe_cap, h->probe_counter, h->cfg.rho0, h->cur));
+  return LBM_OK;
+}
+
+int coarse_step(lbm_ctx* h, bool launch) {
+  int rc = advance(h, 0, nullptr, launch);
+  if (rc) return rc;
+  return probe_launch(h, launch);
+}
+
+// History set-up after initialisation: slots t and t+1 <- (drho, u, 0).
+int seed_history(lbm_ctx* h) {
+  const bool launch = true;
+  h->cur = h->stream;
+  for (int l = 1; l < h->nlev; ++l) {
+    Level& p = h->lev[l - 1];
+    LAUNCH(h->ops.capture(p.view, h->lev[l].ring, h->cfg.storage, p.last, 1, (float)h->cfg.rho0,
+                          h->cur));
+  }
+  h->seeded = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument or level layout";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return g_errmsg[0] ? g_errmsg : "CUDA error";
+    case LBM_EUNSTABLE: return "non-finite mass: the run is unstable";
+    case LBM_ESTATE: return "call out of order (initialise every level and run first)";
+    default: return "unknown error";
+  }
+}
+
+int lbm_lattice(int lattice, int* xi, double* w) {
+  if (!xi || !w) return LBM_EINVAL;
+  auto fill = [&](auto L) {
+    using LT = decltype(L);
+    for (int i = 0; i < LT::Q; ++i) {
+      for (int a = 0; a < 3; ++a) xi[3 * i + a] = LT::c(i, a);
+      w[i] = LT::w(i);
+    }
+    return LT::Q;
+  };
+  switch (lattice) {
+    case LBM_D2Q9: return fill(D2Q9{});
+    case LBM_D3Q19: return fill(D3Q19{});
+    case LBM_D3Q27: return fill(D3Q27{});
+    default: return LBM_EINVAL;
+  }
+}
+
+int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
+               lbm_handle* out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!cfg) return LBM_EINVAL;
+  if (cfg->lattice < 0 || cfg->lattice > 2 || cfg->collision < 0 || cfg->collision > 2 ||
+      cfg->storage < 0 || cfg->storage > 1 || cfg->nlevels < 1 ||
+      cfg->nlevels > LBM_MAX_LEVELS || cfg->batch < 1 || !(cfg->tau0 > 0.5) ||
+      !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau0))
+    return LBM_EINVAL;
+  if (alloc && (!alloc->alloc || !alloc->free)) return LBM_EINVAL;
+  lbm_ctx* h = new (std::nothrow) lbm_ctx();
+  if (!h) return LBM_ENOMEM;
+  h->cfg = *cfg;
+  h->ops = ops_for(cfg->lattice);
+  h->q = h->ops.q;
+  h->D = h->ops.d;
+  h->nlev = cfg->nlevels;
+  h->batch = cfg->batch;
+  h->stream = (cudaStream_t)stream;
+  h->cur = h->stream;
+  if (alloc) {
+    h->has_alloc = true;
+    h->alloc = *alloc;
+  }
+  int rc = build_layout(h);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  for (int l = 0; l < h->nlev; ++l) {
+    const Level& v = h->lev[l];
+    // launch-grid limits of the level update (grid.y, grid.z)
+    if ((long long)v.n[2] * h->batch > 65535 || (v.n[1] + 3) / 4 > 65535 || h->batch > 65535) {
+      delete h;
+      return LBM_EINVAL;
+    }
+  }
+  for (int l = 0; l < h->nlev; ++l) build_view(h, l);
+  for (int l = 1; l < h->nlev; ++l) build_interface(h, l);
+  // device memory
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& v = h->lev[l];
+    v.mem = h->dalloc(v.bytes);
+    if (!v.mem) {
+      release(h);
+      delete h;
+      return LBM_ENOMEM;
+    }
+    v.view.f = v.mem;
+    if (cudaMemsetAsync(v.mem, 0, v.bytes, h->stream) != cudaSuccess) {
+      release(h);
+      delete h;
+      return LBM_ECUDA;
+    }
+    if (l >= 1) {
+      size_t hb = sizeof(float) * 3 * (size_t)v.ring.nv * (size_t)v.ring.K * h->batch;
+      v.hist_mem = h->dalloc(hb);
+      if (!v.hist_mem) {
+        release(h);
+        delete h;
+        return LBM_ENOMEM;
+      }
+      v.ring.hist = (float*)v.hist_mem;
+      cudaMemsetAsync(v.hist_mem, 0, hb, h->stream);
+    }
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    release(h);
+    delete h;
+    return LBM_ECUDA;
+  }
+  h->inited.assign((size_t)h->nlev * h->batch, 0);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    release(h);
+    delete h;
+    return LBM_ECUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_level_info(lbm_handle h, int level, int* n, double* tau, long long* n_active) {
+  if (!h || level < 0 || level >= h->nlev) return LBM_EINVAL;
+  const Level& v = h->lev[level];
+  if (n)
+    for (int a = 0; a < 3; ++a) n[a] = v.n[a];
+  if (tau) *tau = v.tau;
+  if (n_active) *n_active = v.n_active;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* u) {
+  if (!h || level < 0 || level >= h->nlev || run < 0 || run >= h->batch || !rho || !u)
+    return LBM_EINVAL;
+  if (h->ready) {
+    // a new initial state: every level of every run must be set again
+    std::fill(h->inited.begin(), h->inited.end(), 0);
+    h->ready = false;
+  }
+  Level& v = h->lev[level];
+  const long long N = v.n_nodes;
+  double* d = (double*)h->dalloc(sizeof(double) * 4 * N);
+  if (!d) return LBM_ENOMEM;
+  int rc = LBM_OK;
+  do {
+    if (cudaMemcpyAsync(d, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream) ||
+        cudaMemcpyAsync(d + N, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream)) {
+      rc = LBM_ECUDA;
+      break;
+    }
+    cudaError_t e = h->ops.init(v.view, h->cfg.storage, run, d, d + N, h->cfg.rho0, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      snprintf(g_errmsg, sizeof(g_errmsg), "init: %s", cudaGetErrorString(e));
+      rc = LBM_ECUDA;
+    }
+    ++h->launches;
+  } while (0);
+  h->dfree(d);
+  if (rc) return rc;
+  h->inited[(size_t)level * h->batch + run] = 1;
+  if (std::all_of(h->inited.begin(), h->inited.end(), [](char c) { return c != 0; })) {
+    for (int l = 0; l < h->nlev; ++l) {
+      h->lev[l].last = 0;
+      h->lev[l].nsteps = 0;
+    }
+    h->coarse_steps = 0;
+    h->seeded = false;
+    h->ready = true;
+  }
+  return LBM_OK;
+}
+
+int lbm_set_graphs(lbm_handle h, int enable) {
+  if (!h) return LBM_EINVAL;
+  h->use_graphs = enable != 0;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int n_coarse) {
+  if (!h || n_coarse < 0) return LBM_EINVAL;
+  if (!h->ready) return LBM_ESTATE;
+  if (!h->seeded) {
+    int rc = seed_history(h);
+    if (rc) return rc;
+  }
+  for (int s = 0; s < n_coarse; ++s) {
+    if (h->coarse_steps == 0 || !h->use_graphs || h->profiling) {
+      h->cur = h->stream;
+      int rc = coarse_step(h, true);
+      if (rc) return rc;
+    } else {
+      const int key = 1 - h->lev[0].last;
+      if (!h->exec[key]) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        h->cur = h->cap_stream;
+        const long long before = h->launches;
+        int rc = coarse_step(h, true);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        h->cur = h->stream;
+        h->launches = before;  // counted when the graph runs
+        if (rc) {
+          if (g) cudaGraphDestroy(g);
+          return rc;
+        }
+        CK(e);
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        e = cudaGraphInstantiate(&h->exec[key], g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        h->exec_nodes[key] = (long long)nn;
+      } else {
+        int rc = coarse_step(h, false);
+        if (rc) return rc;
+      }
+      CK(cudaGraphLaunch(h->exec[key], h->stream));
+      h->launches += h->exec_nodes[key];
+    }
+    ++h->coarse_steps;
+  }
+  return LBM_OK;
+}
+
+int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
+  if (!h || level < 0 || level >= h->nlev || run < 0 || run >= h->batch || !rho || !u)
+    return LBM_EINVAL;
+  if (!h->ready) return LBM_ESTATE;
+  const Level& v = h->lev[level];
+  const long long N = v.n_nodes;
+  double* d = (double*)h->dalloc(sizeof(double) * 4 * N);
+  if (!d) return LBM_ENOMEM;
+  cudaError_t e = h->ops.macros_d(v.view, h->cfg.storage, run, v.last, d, d + N, h->cfg.rho0,
+                                  h->stream);
+  ++h->launches;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rho, d, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(u, d + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->dfree(d);
+  if (e != cudaSuccess) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "macros: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+int lbm_macros_device(lbm_handle h, int level, int run, float* rho_dev, float* u_dev) {
+  if (!h || level < 0 || level >= h->nlev || run < 0 || run >= h->batch || !rho_dev || !u_dev)
+    return LBM_EINVAL;
+  if (!h->ready) return LBM_ESTATE;
+  const Level& v = h->lev[level];
+  CK(h->ops.macros_f(v.view, h->cfg.storage, run, v.last, rho_dev, u_dev, h->cfg.rho0,
+                     h->stream));
+  ++h->launches;
+  return LBM_OK;
+}
+
+int lbm_populations(lbm_handle h, int level, int run, double* g) {
+  if (!h || level < 0 || level >= h->nlev || run < 0 || run >= h->batch || !g)
+    return LBM_EINVAL;
+  if (!h->ready) return LBM_ESTATE;
+  const Level& v = h->lev[level];
+  const size_t bytes = sizeof(double) * h->q * (size_t)v.n_nodes;
+  double* d = (double*)h->dalloc(bytes);
+  if (!d) return LBM_ENOMEM;
+  cudaError_t e = h->ops.populations(v.view, h->cfg.storage, run, v.last, d, h->stream);
+  ++h->launches;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->dfree(d);
+  if (e != cudaSuccess) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "populations: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+int lbm_probe_add(lbm_handle h, int level, int n, const int* ijk) {
+  if (!h || level < 0 || level >= h->nlev || n < 0 || (n > 0 && !ijk) || n > 4096)
+    return LBM_EINVAL;
+  const Level& v = h->lev[level];
+  for (int k = 0; k < n; ++k)
+    for (int a = 0; a < 3; ++a)
+      if (ijk[3 * k + a] < 0 || ijk[3 * k + a] >= v.n[a]) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  h->dfree(h->probe_ijk);
+  h->dfree(h->probe_rec);
+  h->dfree(h->probe_counter);
+  h->probe_ijk = nullptr;
+  h->probe_rec = nullptr;
+  h->probe_counter = nullptr;
+  h->probe_n = 0;
+  if (n == 0) return LBM_OK;
+  long long per_step = (long long)h->batch * n * 4;
+  long long cap = std::min<long long>(65536, std::max<long long>(16, (1LL << 26) / per_step));
+  h->probe_ijk = (int*)h->dalloc(sizeof(int) * 3 * n);
+  h->probe_rec = (double*)h->dalloc(sizeof(double) * per_step * cap);
+  h->probe_counter = (unsigned long long*)h->dalloc(sizeof(unsigned long long));
+  if (!h->probe_ijk || !h->probe_rec || !h->probe_counter) return LBM_ENOMEM;
+  CK(cudaMemcpyAsync(h->probe_ijk, ijk, sizeof(int) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->probe_counter, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->probe_level = level;
+  h->probe_n = n;
+  h->probe_cap = (int)cap;
+  return LBM_OK;
+}
+
+int lbm_probe(lbm_handle h, double* out, int max_steps, int* n_steps) {
+  if (!h || !n_steps || max_steps < 0 || (max_steps > 0 && !out)) return LBM_EINVAL;
+  *n_steps = 0;
+  if (h->probe_n <= 0) return LBM_OK;
+  unsigned long long cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, h->probe_counter, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const long long kept = std::min<long long>((long long)cnt, h->probe_cap);
+  const long long take = std::min<long long>(kept, max_steps);
+  const long long per_step = (long long)h->batch * h->probe_n * 4;
+  for (long long s = 0; s < take; ++s) {
+    const unsigned long long step = cnt - take + s;
+    const long long slot = (long long)(step % (unsigned long long)h->probe_cap);
+    CK(cudaMemcpyAsync(out + s * per_step, h->probe_rec + slot * per_step,
+                       sizeof(double) * per_step, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaMemsetAsync(h->probe_counter, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *n_steps = (int)take;
+  return LBM_OK;
+}
+
+int lbm_diag(lbm_handle h, int run, double* mass, double* mom) {
+  if (!h || run < 0 || run >= h->batch || !mass || !mom) return LBM_EINVAL;
+  if (!h->ready) return LBM_ESTATE;
+  int rc = LBM_OK;
+  for (int l = 0; l < h->nlev && rc == LBM_OK; ++l) {
+    const Level& v = h->lev[l];
+    const int nb = (int)((v.n_nodes + kDiagThreads - 1) / kDiagThreads);
+    double* part = (double*)h->dalloc(sizeof(double) * 4 * nb);
+    if (!part) return LBM_ENOMEM;
+    std::vector<double> hp((size_t)4 * nb);
+    cudaError_t e = h->ops.diag_partial(v.view, h->cfg.storage, run, v.last, part, nb, h->stream);
+    ++h->launches;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost,
+                          h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->dfree(part);
+    if (e != cudaSuccess) {
+      snprintf(g_errmsg, sizeof(g_errmsg), "diag: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+    // block partials summed in a fixed order on the host
+    double s[4] = {0, 0, 0, 0};
+    for (int j = 0; j < 4; ++j)
+      for (int b = 0; b < nb; ++b) s[j] += hp[(size_t)j * nb + b];
+    mass[l] = s[0];
+    for (int a = 0; a < 3; ++a) mom[3 * l + a] = s[1 + a];
+    for (int j = 0; j < 4; ++j)
+      if (!std::isfinite(s[j])) rc = LBM_EUNSTABLE;
+  }
+  return rc;
+}
+
+int lbm_sync(lbm_handle h) {
+  if (!h) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+long long lbm_kernel_launches(lbm_handle h) { return h ? h->launches : -1; }
+
+int lbm_profile(lbm_handle h, int enable) {
+  if (!h) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  h->recs.clear();
+  h->pool_used = 0;
+  h->profiling = enable != 0;
+  return LBM_OK;
+}
+
+int lbm_profile_read(lbm_handle h, int kind, int level, double* total_ms, long long* count) {
+  if (!h || !total_ms || !count) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  double t = 0.0;
+  long long n = 0;
+  for (const auto& r : h->recs) {
+    if (r.kind != kind || (level >= 0 && r.level != level)) continue;
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    t += ms;
+    ++n;
+  }
+  *total_ms = t;
+  *count = n;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle h) {
+  if (!h) return;
+  release(h);
+  delete h;
+}
+
+}  // extern "C"
