@@ -140,15 +140,35 @@ def test_batch_runs_independent(M):
             assert np.array_equal(r1, r2, equal_nan=True) and np.array_equal(u1, u2, equal_nan=True)
 
 
-def test_fp16_shifted_storage_bound(M):
-    """binary16 storage of g = f - w rho0 with binary32 arithmetic: error
-    against the FP64 oracle stays below 5e-5 (rho) / 5e-5 (u) on this case."""
-    case = W.small_2level_2d("RR", steps=30)
+def fp16_bound(case, o_initial):
+    """Stated error bound of binary16 shifted storage: every stored
+    population is rounded to nearest, at most half an ulp of the largest
+    stored magnitude gmax (2^-11 gmax relative spacing), once per update of
+    the finest level; the roundings are unbiased, so they accumulate like a
+    random walk over the n = 2^(L-1) * steps finest updates.  rho and u sum
+    q such roundings (weights <= 1): bound = 2 * q^(1/2) * 2^-11 * gmax *
+    n^(1/2), with a factor 2 of margin."""
+    _, w = oracle.lattice(case.lattice)
+    gmax = 0.0
+    for l in range(case.nlevels):
+        f = o_initial.populations(l)
+        gmax = max(gmax, float(np.max(np.abs(f - w[:, None] * case.rho0))))
+    n = case.steps * 2 ** (case.nlevels - 1)
+    return 2.0 * np.sqrt(case.q) * 2.0 ** -11 * gmax * np.sqrt(n)
+
+
+@pytest.mark.parametrize("mk", [lambda: W.small_2level_2d("RR", steps=30),
+                                lambda: W.small_3d("D3Q19", "RR", nlevels=2, steps=5)])
+def test_fp16_shifted_storage_bound(M, mk):
+    """binary16 storage of g = f - w rho0 with binary32 arithmetic stays
+    within the stated bound of the FP64 oracle."""
+    case = mk()
     g = M.Lbm.from_case(case, storage="fp16")
     o = oracle.Run.from_case(case)
+    tol = fp16_bound(case, o)
     g.step(case.steps)
     o.step(case.steps)
-    compare(g, o, 2, tol=5e-5)
+    compare(g, o, case.nlevels, tol=tol)
 
 
 def test_rest_state_exact(M):
