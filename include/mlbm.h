@@ -178,6 +178,24 @@ int lbm_probe(lbm_handle h, double* out, int max_steps, int* n_steps);
  * Returns LBM_EUNSTABLE if any sum is not finite.  Synchronises. */
 int lbm_diag(lbm_handle h, int run, double* mass, double* mom);
 
+/* Same result as lbm_diag, computed without allocating anything.  The paper
+ * has no counterpart: this serves callers that cannot let the library
+ * allocate device memory -- a serving loop bound to a fixed device-memory
+ * budget, a process whose device memory belongs to another framework's
+ * pool, or a monitor that cannot take the device-wide synchronisation of
+ * cudaFree.  The partial sums live in one fixed device array of 2 MiB inside
+ * the library (held by every GPU that loads the library until the process
+ * exits).  Limit: every level of the run must have at most 16,777,216 nodes
+ * (2^24); a run with a larger level is rejected with LBM_EINVAL before any
+ * device work.  The first call on a device looks the array's address up
+ * once for that device (so make that first call with the handle's device
+ * current and before any stream capture).  All calls share the one array:
+ * calls whose device work overlaps in time (different streams, or several
+ * handles at once) race and must be serialised by the caller; nothing in the
+ * array needs clearing, because every call writes each value before reading
+ * it.  Synchronises. */
+int lbm_diag_noalloc(lbm_handle h, int run, double* mass, double* mom);
+
 /* Block until all work issued by the handle has finished. */
 int lbm_sync(lbm_handle h);
 

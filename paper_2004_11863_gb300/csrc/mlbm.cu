@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -829,3 +830,88 @@ void lbm_destroy(lbm_handle h) {
 }
 
 }  // extern "C"
+
+// ======================================================================
+// lbm_diag_noalloc: the conservation diagnostic without any allocation.
+//
+// lbm_diag obtains a temporary device buffer for its per-block partial sums
+// on every call.  Some callers cannot let the library allocate: a serving
+// loop that admits runs against a fixed device-memory budget and must not
+// grow after admission, a host whose device memory is entirely handed to
+// another framework's caching pool, or a monitor that cannot afford the
+// device-wide synchronisation that cudaFree implies.  This variant keeps the
+// partial sums in one fixed array that lives in the library's device image
+// for as long as the library is loaded (every GPU that loads the library
+// holds it until the process exits).
+// ======================================================================
+namespace {
+
+// Room for the per-block partials of a level of up to this many nodes
+// (kDiagThreads nodes per block, 4 sums per block) plus the final sums.
+constexpr long long kNoAllocMaxNodes = 16777216LL;  // 2^24
+constexpr int kNoAllocMaxBlocks = (int)(kNoAllocMaxNodes / kDiagThreads);
+constexpr int kNoAllocSlots = 4 * kNoAllocMaxBlocks + 4;
+
+static __device__ __align__(256) double g_diag_scratch[kNoAllocSlots];
+
+// Final sums of the block partials, one thread per quantity, in block order
+// (the same order lbm_diag uses on the host, so both give the same bits).
+__global__ void k_diag_final(const double* partial, int nblocks, double* out) {
+  const int j = threadIdx.x;
+  if (j >= 4) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(long long)j * nblocks + b];
+  out[j] = s;
+}
+
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {};
+
+// Address of the scratch array on the current device, looked up once per
+// device.
+int scratch_on_current_device(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return LBM_EINVAL;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_diag_scratch));
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<double*>(g_scratch_ptr[dev]);
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_diag_noalloc(lbm_handle h, int run, double* mass, double* mom) {
+  if (!h || run < 0 || run >= h->batch || !mass || !mom) return LBM_EINVAL;
+  for (int l = 0; l < h->nlev; ++l)
+    if (h->lev[l].n_nodes > kNoAllocMaxNodes) return LBM_EINVAL;  // beyond the fixed scratch
+  if (!h->ready) return LBM_ESTATE;
+  double* scratch = nullptr;
+  int rc = scratch_on_current_device(&scratch);
+  if (rc) return rc;
+  double* partial = scratch;
+  double* result = scratch + 4 * (long long)kNoAllocMaxBlocks;
+  rc = LBM_OK;
+  for (int l = 0; l < h->nlev; ++l) {
+    const Level& v = h->lev[l];
+    const int nb = (int)((v.n_nodes + kDiagThreads - 1) / kDiagThreads);
+    // every partial the final sum reads is written first, so nothing needs
+    // clearing between calls
+    CK(h->ops.diag_partial(v.view, h->cfg.storage, run, v.last, partial, nb, h->stream));
+    k_diag_final<<<1, 32, 0, h->stream>>>(partial, nb, result);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    double s[4];
+    CK(cudaMemcpyAsync(s, result, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    mass[l] = s[0];
+    for (int a = 0; a < 3; ++a) mom[3 * l + a] = s[1 + a];
+    for (int j = 0; j < 4; ++j)
+      if (!std::isfinite(s[j])) rc = LBM_EUNSTABLE;
+  }
+  return rc;
+}

@@ -79,6 +79,7 @@ def lib():
     L.lbm_probe_add.argtypes = [P, ctypes.c_int, ctypes.c_int, ip]
     L.lbm_probe.argtypes = [P, dp, ctypes.c_int, ip]
     L.lbm_diag.argtypes = [P, ctypes.c_int, dp, dp]
+    L.lbm_diag_noalloc.argtypes = [P, ctypes.c_int, dp, dp]
     L.lbm_sync.argtypes = [P]
     L.lbm_kernel_launches.argtypes = [P]
     L.lbm_kernel_launches.restype = ctypes.c_longlong
@@ -253,6 +254,26 @@ class Lbm:
         rc = lib().lbm_diag(self._h, run, _dp(mass), _dp(mom))
         if rc not in (LBM_OK, -4):
             _check(rc, "lbm_diag")
+        return mass, mom, rc == LBM_OK
+
+    NOALLOC_MAX_NODES = 1 << 24
+
+    def diag_noalloc(self, run=0):
+        """lbm_diag without any allocation, for callers that cannot let the
+        library allocate device memory (fixed memory budget, device memory
+        owned by another pool, no room for cudaFree's synchronisation).
+        Uses one fixed 2 MiB device array shared by every call: serialise
+        calls that could overlap on the GPU.  Levels are limited to 2^24
+        nodes."""
+        for l in range(self.nlevels):
+            if self.nodes(l) > self.NOALLOC_MAX_NODES:
+                raise ValueError(f"level {l} has {self.nodes(l)} nodes; lbm_diag_noalloc "
+                                 f"handles at most {self.NOALLOC_MAX_NODES}")
+        mass = np.zeros(self.nlevels)
+        mom = np.zeros((self.nlevels, 3))
+        rc = lib().lbm_diag_noalloc(self._h, run, _dp(mass), _dp(mom))
+        if rc not in (LBM_OK, -4):
+            _check(rc, "lbm_diag_noalloc")
         return mass, mom, rc == LBM_OK
 
     def sync(self):
