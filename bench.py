@@ -246,7 +246,8 @@ def main():
         fields.append((rp, up))
 
     g = mlbm.Lbm(case.lattice, case.collision, case.tau0, case.dims, case.boxes,
-                 storage=args.storage, batch=batch, rho0=case.rho0, stream=stream.cuda_stream)
+                 storage=args.storage, batch=batch, rho0=case.rho0, stream=stream.cuda_stream,
+                 u_ref=case.u_ref)
     for l in range(case.nlevels):
         for b in range(batch):
             g.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
@@ -298,26 +299,66 @@ def main():
     shares = {k: round(v[0] / args.steps / step_total, 4) for k, v in kt.items()}
 
     # ---------------- end to end through the C ABI with host buffers -------
+    # Initial fields uploaded from pinned host memory, then every coarse step
+    # followed by a device-to-host read of that step's result: the probe
+    # samples (rho, u at 16 probe nodes of the fine level, every run), the
+    # time series the paper's noise analysis is built on; finally the
+    # macroscopic fields of every level and run are read back.
     torch.cuda.synchronize()
-    outs = [(torch.empty(fields[l][0].shape, dtype=torch.float64).pin_memory(),
-             torch.empty(fields[l][1].shape, dtype=torch.float64).pin_memory())
-            for l in range(case.nlevels)]
+    n1 = W.level_layout(case)[-1]["n"]
+    probes = [[int(n1[0] * (k + 1) / 17), int(n1[1] / 2), int(n1[2] / 2)] for k in range(16)]
+    g.probe_add(case.nlevels - 1, probes)
     t0 = time.perf_counter()
     for l in range(case.nlevels):
         for b in range(batch):
             g.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
-    g.step(args.steps)
+    d2h_probe = 0
+    for _ in range(args.steps):
+        g.step(1)
+        rec = g.probe(max_steps=1)
+        d2h_probe += rec.nbytes
     for l in range(case.nlevels):
         for b in range(batch):
-            rho, u = g.macros(l, b)
+            g.macros(l, b)
     e2e_s = time.perf_counter() - t0
     h2d = sum(4 * fields[l][0].numel() * 8 for l in range(case.nlevels)) * batch
-    d2h = h2d
+    d2h = h2d + d2h_probe
     e2e = {"value": round(U * batch * ws * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
-           "note": f"lbm_init from pinned host fields, {args.steps} coarse steps, lbm_macros of "
-                   f"every level and run back to the host"}
+           "note": f"lbm_init of every level and run from pinned host fields, then {args.steps} x "
+                   f"(lbm_step 1 + lbm_probe read-back of 16 probes x {batch} runs), then "
+                   f"lbm_macros of every level and run; bytes amortised per step"}
     g.close()
+
+    # ---------------- variants of the same workload (same batch) ------------
+    variants = {}
+    for vname, st, coll in (("fp16_shifted_rr", "fp16", case.collision),
+                            ("fp32_shifted_bgk", "fp32", "BGK")):
+        if vname.startswith(args.storage) and coll == case.collision:
+            continue
+        gv = mlbm.Lbm(case.lattice, coll, case.tau0, case.dims, case.boxes, storage=st,
+                      batch=batch, rho0=case.rho0, stream=stream.cuda_stream, u_ref=case.u_ref)
+        for l in range(case.nlevels):
+            for b in range(batch):
+                gv.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
+        gv.step(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        gv.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        vms = ev0.elapsed_time(ev1)
+        gv.profile(True)
+        gv.step(args.steps)
+        vt, vn = gv.profile_read(0, dom_level)
+        gv.profile(False)
+        vs = 2 if st == "fp16" else 4
+        vb = counts[dom_level] * batch * 2 * case.q * vs
+        variants[vname] = {"value": round(U * batch * ws * args.steps / (vms * 1e-3) / 1e6, 1),
+                           "unit": "MLUPS",
+                           "dominant_kernel_gbs": round(vb / (vt / vn * 1e-3) / 1e9, 1),
+                           "dominant_kernel_frac": round(vb / (vt / vn * 1e-3) / 1e9 / peak, 4)}
+        gv.close()
 
     if rank != 0:
         return
@@ -347,6 +388,7 @@ def main():
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "e2e": e2e,
+        "variants": variants,
         "cpu_baseline": cpu,
         "stable": bool(stable),
     }

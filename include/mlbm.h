@@ -17,8 +17,9 @@
  *     (eq. rescTau).
  *
  * Every step runs in hand-written CUDA kernels for sm_103a.  Populations are
- * stored per level as structure-of-arrays planes of g_i = f_i - w_i rho0
- * (FP32 or FP16), streamed in place with the AA pattern.
+ * stored per level as structure-of-arrays planes of g_i = f_i - f0_i(rho0, U)
+ * (FP32 or FP16; U = 0 is the rest-state shift f_i - w_i rho0), streamed in
+ * place with the AA pattern.
  *
  * General rules
  *   - Every function returns 0 on success or a negative LBM_E* code; no
@@ -92,6 +93,12 @@ typedef struct {
   lbm_box box[LBM_MAX_LEVELS - 1];
   int batch;     /* independent runs sharing this layout (>= 1); each run
                     has its own populations and initial state */
+  double u_ref[3]; /* velocity U of the reference state: populations are
+                      stored as g_i = f_i - f0_i(rho0, U).  {0,0,0} gives the
+                      rest-state shift f_i - w_i rho0; setting U to the flow's
+                      mean (free-stream) velocity keeps the stored values, and
+                      their rounding, small.  |U| components <= 0.5; U_z = 0
+                      for D2Q9.  Results do not depend on U beyond rounding. */
 } lbm_config;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
@@ -110,8 +117,9 @@ typedef struct {
  *     periodic seam) and at least 4 parent cells must stay outside; inside a
  *     bounded parent axis, lo >= 4 and hi <= parent count - 5 (nesting
  *     margin of four parent cells);
- *   - tau0 > 1/2, batch >= 1, and (node count along z) x batch <= 65535
- *     on every level.
+ *   - tau0 > 1/2, batch >= 1, (node count along z) x batch <= 65535 and
+ *     fewer than 2^31 stored elements (nodes plus padding) per population
+ *     plane on every level.
  * `stream` is a cudaStream_t (NULL = legacy default stream).  `alloc` may be
  * NULL.  On success *out receives the handle; on error *out is NULL and no
  * memory is held.  The new run must be initialised with lbm_init on every
@@ -152,9 +160,9 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u);
 int lbm_macros_device(lbm_handle h, int level, int run, float* rho_dev,
                       float* u_dev);
 
-/* Post-collision shifted populations g_i = f_i - w_i rho0 of one level of
- * one run, host [q][N] doubles, in the library's velocity order (returned
- * by lbm_lattice).  Synchronises. */
+/* Post-collision populations of one level of one run, shifted by the rest
+ * state (f_i - w_i rho0, whatever u_ref is), host [q][N] doubles, in the
+ * library's velocity order (returned by lbm_lattice).  Synchronises. */
 int lbm_populations(lbm_handle h, int level, int run, double* g);
 
 /* The library's velocity set: xi host [q][3] ints, w host [q] doubles.

@@ -536,6 +536,7 @@ int orc_init_level(orc_run* r, int level, const double* rho, const double* u) {
   if (level < 0 || level >= r->nlev) return -1;
   level_t* v = &r->lev[level];
   const int q = r->L.q;
+#pragma omp parallel for schedule(static)
   for (long id = 0; id < v->N; ++id) {
     double uu[3] = {u[id], u[v->N + id], u[2 * v->N + id]};
     feq_lat(&r->L, rho[id], uu, v->fpost + id * q);
@@ -767,6 +768,7 @@ int orc_macros(const orc_run* r, int level, double* rho, double* u) {
   if (level < 0 || level >= r->nlev) return -1;
   const level_t* v = &r->lev[level];
   const int q = r->L.q;
+#pragma omp parallel for schedule(static)
   for (long id = 0; id < v->N; ++id) {
     if (v->cls[id] == C_INACTIVE) {
       rho[id] = NAN;

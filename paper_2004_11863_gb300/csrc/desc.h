@@ -27,12 +27,19 @@ struct LevelView {
   int ina_lo[3], ina_hi[3];
 };
 
+// Reference state of the shifted storage: level arrays hold
+// g_i = f_i - f0_i(rho0, U) (U = 0: the rest-state shift f_i - w_i rho0).
+struct RefState {
+  double rho0;
+  double U[3];
+};
+
 constexpr int kMaxFaces = 6;
 
 // Threads per block of the FP64 diagnostic reduction.
 constexpr int kDiagThreads = 256;
 
-// Parent-level history of (drho, u_x, u_y, u_z, f1_0 .. f1_{q-1}) on the
+// Parent-level history of (drho, du_x, du_y, du_z, f1_0 .. f1_{q-1}) on the
 // surface of a child box, extended by one parent cell past its edges, in
 // three time slots (t-1, t, t+1).  Face f (axis[f], side[f]) has ext[f][a]
 // entries along axis a; local index i_a maps to parent coordinate
@@ -62,6 +69,18 @@ struct BndDesc {
   int axis[kMaxFaces], side[kMaxFaces];
   long long start[kMaxFaces + 1];
   int lo[kMaxFaces][3], ext[kMaxFaces][3];
+};
+
+// Face tiles of the child boundary for the tiled coarse -> fine rebuild:
+// face f (axis[f], side[f]) spans the child nodes of the two tangent axes
+// t1[f] < t2[f] (t2 = 2 with one node in 2D), cut into ntile1[f] x ntile2[f]
+// tiles; tiles of face f are blocks tstart[f] .. tstart[f+1]-1.
+struct InjDesc {
+  int nf;
+  int axis[kMaxFaces], side[kMaxFaces], t1[kMaxFaces], t2[kMaxFaces];
+  int ntile1[kMaxFaces], ntile2[kMaxFaces];
+  long long tstart[kMaxFaces + 1];
+  int boxed[3];
 };
 
 // Parent-level f->c nodes (TN, the parent nodes one parent cell inside the

@@ -5,8 +5,9 @@
 //   k_capture         parent pre-collision (drho, u, f^(1)) at t+1 on a child
 //                     box surface -> three-slot history (steps 2a/2b, 2g);
 //   k_inject          child TF / IE nodes: temporal (eq. TempInt) and spatial
-//                     (eq. spaceInt) interpolation, rescaling (eq. rescff),
-//                     written where the child's next update reads them;
+//                     (eq. spaceInt) interpolation staged per face tile in
+//                     shared memory, rescaling (eq. rescff), written where
+//                     the child's next update reads them;
 //   k_restrict        parent TN nodes: filtered child f^(1) (eq. filterFneq),
 //                     rescaling (eq. rescfc), written where the parent's next
 //                     update reads them (step 3d);
@@ -31,32 +32,36 @@ namespace mlbm {
 
 __device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
-// Element offsets of a node and of its 3^D neighbours inside a plane.
+// binary32 reference with its per-direction constants (formed on the host
+// by make_ref_f in the launch wrappers)
+
+// Element offsets of a node and of its 3^D neighbours inside a plane
+// (32-bit: the host keeps every plane below 2^31 elements; plane bases are
+// formed in 64 bits from warp-uniform values).
 struct NodeAddr {
-  long long zo[3];
+  int zo[3];
   int yo[3];
   int xo[3];
-  long long off;
-  __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
-    return off + zo[dz + 1] + yo[dy + 1] + xo[dx + 1];
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    return zo[dz + 1] + yo[dy + 1] + xo[dx + 1];
   }
 };
 
 template <class L>
 __device__ __forceinline__ NodeAddr node_addr(const LevelView& v, int x, int y, int z) {
   NodeAddr a;
-  a.off = v.off;
+  const int off = (int)v.off;
 #pragma unroll
   for (int d = -1; d <= 1; ++d) {
     int xx = x + d, yy = y + d;
     if (v.per[0]) xx = wrapi(xx, v.n[0]);
     if (v.per[1]) yy = wrapi(yy, v.n[1]);
-    a.xo[d + 1] = xx;
+    a.xo[d + 1] = xx + off;
     a.yo[d + 1] = yy * v.SX;
     if constexpr (L::D == 3) {
       int zz = z + d;
       if (v.per[2]) zz = wrapi(zz, v.n[2]);
-      a.zo[d + 1] = (long long)zz * v.SY * v.SX;
+      a.zo[d + 1] = zz * v.SY * v.SX;
     } else {
       a.zo[d + 1] = 0;
     }
@@ -113,8 +118,43 @@ __device__ __forceinline__ void load_post(const S* f, long long plane, const Nod
 
 // ------------------------------------------------------- K1: level update
 // One thread per node; a warp covers 32 consecutive x of one row.
-template <class L, int COLL, class S, int PAR>
-__global__ void __launch_bounds__(128) k_stream_collide(LevelView v, float omega, float rho0) {
+// Resident blocks per SM the level update is compiled for: the register
+// budget each lattice's collision fits (D2Q9 40, D3Q19 80, D3Q27 96
+// registers per thread; with a moving reference 48, 96, 128).
+template <class L>
+struct K1Occupancy;
+template <>
+struct K1Occupancy<D2Q9> {
+  static constexpr int MINB_MOV = 10;
+#ifdef K1_MINB_D2Q9
+  static constexpr int MINB = K1_MINB_D2Q9;
+#else
+  static constexpr int MINB = 12;
+#endif
+};
+template <>
+struct K1Occupancy<D3Q19> {
+  static constexpr int MINB_MOV = 5;
+#ifdef K1_MINB_D3Q19
+  static constexpr int MINB = K1_MINB_D3Q19;
+#else
+  static constexpr int MINB = 6;
+#endif
+};
+template <>
+struct K1Occupancy<D3Q27> {
+  static constexpr int MINB_MOV = 4;
+#ifdef K1_MINB_D3Q27
+  static constexpr int MINB = K1_MINB_D3Q27;
+#else
+  static constexpr int MINB = 5;
+#endif
+};
+// MOV: the storage is shifted by a moving reference (u_ref != 0); its extra
+// deviation terms get a larger register budget (MINB_MOV resident blocks).
+template <class L, int COLL, class S, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, MOV ? K1Occupancy<L>::MINB_MOV : K1Occupancy<L>::MINB)
+    k_stream_collide(LevelView v, float omega, RefF R) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 4 + threadIdx.y;
   int z = blockIdx.z, run = 0;
@@ -127,29 +167,42 @@ __global__ void __launch_bounds__(128) k_stream_collide(LevelView v, float omega
   S* f = static_cast<S*>(v.f) + run * v.run_stride;
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
-  load_pre<L, S>(f, v.plane, a, PAR, g);
-  collide<L, COLL>(g, omega, rho0);
+#ifdef K1_LDG
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (PAR == 0)
-      Store<S>::st(f + (long long)opp<L>(i) * v.plane + a.at(0, 0, 0), g[i]);
+      g[i] = Store<S>::ldg(f + (long long)i * v.plane + a.at(0, 0, 0));
     else
-      Store<S>::st(f + (long long)i * v.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), g[i]);
+      g[i] = Store<S>::ldg(f + (long long)opp<L>(i) * v.plane +
+                           a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
+  });
+#else
+  load_pre<L, S>(f, v.plane, a, PAR, g);
+#endif
+  collide_emit<L, COLL, MOV>(g, omega, R, [&](auto I, float val) {
+    constexpr int i = decltype(I)::value;
+#ifdef K1_STCS
+    if constexpr (PAR == 0)
+      Store<S>::stcs(f + (long long)opp<L>(i) * v.plane + a.at(0, 0, 0), val);
+    else
+      Store<S>::stcs(f + (long long)i * v.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), val);
+#else
+    if constexpr (PAR == 0)
+      Store<S>::st(f + (long long)opp<L>(i) * v.plane + a.at(0, 0, 0), val);
+    else
+      Store<S>::st(f + (long long)i * v.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), val);
+#endif
   });
 }
 
-// (drho, u, f^(1)) of a population set.
+// (drho, du, f^(1)) of a population set (deviations from the reference).
 template <class L>
-__device__ __forceinline__ void split_neq(const float (&g)[L::Q], float rho0, float& drho,
-                                          float& ux, float& uy, float& uz, float (&f1)[L::Q]) {
-  float jx, jy, jz;
-  moments<L>(g, drho, jx, jy, jz);
-  const float inv = 1.0f / (rho0 + drho);
-  ux = jx * inv;
-  uy = jy * inv;
-  uz = (L::D == 3) ? jz * inv : 0.0f;
+__device__ __forceinline__ void split_neq(const float (&g)[L::Q], const RefF& R, float& drho,
+                                          float& dux, float& duy, float& duz,
+                                          float (&f1)[L::Q]) {
+  deviations<L>(g, R, drho, dux, duy, duz);
   float g0[L::Q];
-  equilibrium<L>(drho, rho0 + drho, ux, uy, uz, g0);
+  equilibrium_f<L>(drho, dux, duy, duz, R, g0);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     f1[i] = g[i] - g0[i];
@@ -163,12 +216,14 @@ __device__ __forceinline__ int ring_face(const long long* start, int nf, long lo
 }
 
 // ------------------------------------------------------------ K2: capture
-// mode 0: shift the slots (t-1 <- t, t <- t+1) and store the parent's
-// pre-collision state for an update of parity `par` into slot t+1.
-// mode 1 (set-up): store (drho, u, 0) of the parent's current state (laid
-// out after an update of parity `par`) into slots t and t+1.
+// The history keeps three slots that rotate: the host passes the slot that
+// receives the newest state.  mode 0: store the parent's pre-collision state
+// for an update of parity `par` into slot `s_new`.  mode 1 (set-up): store
+// (drho, du, 0) of the parent's current state (laid out after an update of
+// parity `par`) into slots `s_new` and `s_also`.
 template <class L, class S>
-__global__ void k_capture(LevelView p, RingDesc R, int par, int mode, float rho0) {
+__global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new, int s_also,
+                          RefF ref) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int run = blockIdx.y;
   if (k >= R.K) return;
@@ -191,175 +246,217 @@ __global__ void k_capture(LevelView p, RingDesc R, int par, int mode, float rho0
     load_pre<L, S>(f, p.plane, a, par, g);
   else
     load_post<L, S>(f, p.plane, a, par, g);
-  float drho, ux, uy, uz, f1[L::Q];
-  split_neq<L>(g, rho0, drho, ux, uy, uz, f1);
+  float drho, dux, duy, duz, f1[L::Q];
+  split_neq<L>(g, ref, drho, dux, duy, duz, f1);
   const int nv = R.nv;
   float* h = R.hist + (long long)run * 3 * nv * R.K;
-  auto slot = [&](int s, int vv) -> float& { return h[((long long)s * nv + vv) * R.K + k]; };
-  if (mode == 0) {
-    for (int vv = 0; vv < nv; ++vv) {
-      slot(0, vv) = slot(1, vv);
-      slot(1, vv) = slot(2, vv);
-    }
-  }
-  float nvv[4] = {drho, ux, uy, uz};
-  for (int s = (mode == 0 ? 2 : 1); s <= 2; ++s) {
+  const float m4[4] = {drho, dux, duy, duz};
+  for (int rep = 0; rep < (mode == 0 ? 1 : 2); ++rep) {
+    float* hs = h + (long long)(rep == 0 ? s_new : s_also) * nv * R.K + k;
 #pragma unroll
-    for (int vv = 0; vv < 4; ++vv) slot(s, vv) = nvv[vv];
+    for (int vv = 0; vv < 4; ++vv) hs[(long long)vv * R.K] = m4[vv];
     sfor<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      slot(s, 4 + i) = (mode == 0) ? f1[i] : 0.0f;
+      hs[(long long)(4 + i) * R.K] = (mode == 0) ? f1[i] : 0.0f;
     });
   }
 }
 
 // ------------------------------------------------------------- K3: inject
-// Child boundary nodes.  wt: temporal weights on slots (t-1, t, t+1);
+// Child TF / IE nodes (the outer node layer of the child box).  wt: temporal
+// weights on the history slots s_m1, s_0, s_p1 holding t-1, t, t+1;
 // resc = tau_f / (2 tau_c) (eq. rescff); par: the child's next update.
+// Organised by face tiles: a block covers TI x TJ
+// child nodes of one face of the child box; it first stages the temporally
+// interpolated parent history (eq. TempInt) of the parent nodes the tile's
+// stencils reach in shared memory, then every thread applies its spatial
+// stencil (eq. spaceInt, tensor product on face centres) from there,
+// rebuilds with eq. rescff and stores.  Each history value is read once per
+// tile instead of once per stencil use.
+template <class L>
+struct InjTile {
+  static constexpr int TI = (L::D == 3) ? 32 : 128;  // along the first tangent axis
+  static constexpr int TJ = (L::D == 3) ? 8 : 1;     // along the second
+  static constexpr int WI = TI / 2 + 5;              // parent window (stencil reach)
+  static constexpr int WJ = (L::D == 3) ? TJ / 2 + 5 : 1;
+  static constexpr int NV = 4 + L::Q;
+};
+
 template <class L, class S>
-__global__ void k_inject(LevelView c, BndDesc B, RingDesc R, float w0, float w1, float w2,
-                         float resc, int par, float rho0) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(InjTile<L>::TI * InjTile<L>::TJ)
+    k_inject(LevelView c, InjDesc J, RingDesc R, float w0, float w1, float w2, int s_m1,
+                   int s_0, int s_p1, float resc, int par, RefF ref) {
+  using T = InjTile<L>;
+  __shared__ float sv[T::NV][T::WJ][T::WI];
   const int run = blockIdx.y;
-  if (k >= B.count) return;
-  const int fc = ring_face(B.start, B.nf, k);
-  long long loc = k - B.start[fc];
-  int X[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int e = B.ext[fc][a];
-    X[a] = B.lo[fc][a] + (int)(loc % e);
-    loc /= e;
-  }
-  // odd child coordinates (at most two, never the face axis)
-  int odd0 = -1, odd1 = -1;
-#pragma unroll
-  for (int a = 0; a < L::D; ++a)
-    if (X[a] & 1) {
-      if (odd0 < 0) odd0 = a;
-      else odd1 = a;
-    }
-  const int n0 = odd0 >= 0 ? 4 : 1, n1 = odd1 >= 0 ? 4 : 1;
-  const float sw[4] = {-1.0f / 16.0f, 9.0f / 16.0f, 9.0f / 16.0f, -1.0f / 16.0f};
-  // ring face of the same (axis, side): strides of its local index
-  const int rf = fc;
+  // tile -> face, tile coordinates
+  int f = 0;
+  while (f + 1 < J.nf && (long long)blockIdx.x >= J.tstart[f + 1]) ++f;
+  const int tile = (int)(blockIdx.x - J.tstart[f]);
+  const int a = J.axis[f], t1 = J.t1[f], t2 = J.t2[f];
+  const int X0 = (tile % J.ntile1[f]) * T::TI;
+  const int Y0 = (tile / J.ntile1[f]) * T::TJ;
+  const int p0i = (X0 >> 1) - 2, p0j = (L::D == 3) ? (Y0 >> 1) - 2 : 0;
   long long stride[3];
   stride[0] = 1;
-  stride[1] = R.ext[rf][0];
-  stride[2] = stride[1] * R.ext[rf][1];
-  const int nv = R.nv;
-  const float* h = R.hist + (long long)run * 3 * nv * R.K;
-  float acc[4 + L::Q];
-#pragma unroll
-  for (int j = 0; j < 4 + L::Q; ++j) acc[j] = 0.0f;
-  for (int s0 = 0; s0 < n0; ++s0)
-    for (int s1 = 0; s1 < n1; ++s1) {
-      long long idx = R.start[rf];
-      float w = 1.0f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (a == R.axis[rf] || a >= L::D) continue;
-        int xc = X[a];
-        if (a == odd0) {
-          xc += 2 * s0 - 3;
-          w *= sw[s0];
-        } else if (a == odd1) {
-          xc += 2 * s1 - 3;
-          w *= sw[s1];
-        }
-        const int half = (xc >= 0) ? xc / 2 : -((-xc) / 2);  // xc is even
-        int li;
-        if (R.boxed[a])
-          li = half + 1;
-        else
-          li = wrapi(half, R.pn[a]);
-        idx += (long long)li * stride[a];
-      }
-#pragma unroll
-      for (int j = 0; j < 4 + L::Q; ++j) {
-        const float v0 = h[((long long)0 * nv + j) * R.K + idx];
-        const float v1 = h[((long long)1 * nv + j) * R.K + idx];
-        const float v2 = h[((long long)2 * nv + j) * R.K + idx];
-        acc[j] += w * (w0 * v0 + w1 * v1 + w2 * v2);
+  stride[1] = R.ext[f][0];
+  stride[2] = stride[1] * R.ext[f][1];
+  const float* h = R.hist + (long long)run * 3 * R.nv * R.K;
+  const long long K = R.K, nv = R.nv;
+  // stage: parent window x values, interpolated in time
+  const int nthr = T::TI * T::TJ;
+  const int tid = threadIdx.y * T::TI + threadIdx.x;
+#pragma unroll 4
+  for (int e = tid; e < T::NV * T::WJ * T::WI; e += nthr) {
+    const int pi = e % T::WI, pj = (e / T::WI) % T::WJ, vv = e / (T::WI * T::WJ);
+    int ri = p0i + pi, rj = p0j + pj;  // parent coordinates relative to the box / absolute
+    bool ok = true;
+    long long idx = R.start[f];
+    // first tangent axis
+    if (R.boxed[t1]) {
+      ok = ok && ri >= -1 && ri <= R.ext[f][t1] - 2;
+      idx += (long long)(ri + 1) * stride[t1];
+    } else {
+      ri = ((ri % R.pn[t1]) + R.pn[t1]) % R.pn[t1];
+      idx += (long long)ri * stride[t1];
+    }
+    if (L::D == 3) {
+      if (R.boxed[t2]) {
+        ok = ok && rj >= -1 && rj <= R.ext[f][t2] - 2;
+        idx += (long long)(rj + 1) * stride[t2];
+      } else {
+        rj = ((rj % R.pn[t2]) + R.pn[t2]) % R.pn[t2];
+        idx += (long long)rj * stride[t2];
       }
     }
+    float val = 0.0f;
+    if (ok)
+      val = w0 * h[((long long)s_m1 * nv + vv) * K + idx] +
+            w1 * h[((long long)s_0 * nv + vv) * K + idx] +
+            w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+    sv[vv][pj][pi] = val;
+  }
+  __syncthreads();
+  const int xi = X0 + (int)threadIdx.x, xj = Y0 + (int)threadIdx.y;
+  if (xi >= c.n[t1] || (L::D == 3 && xj >= c.n[t2])) return;
+  int X[3];
+  X[a] = J.side[f] ? c.n[a] - 1 : 0;
+  X[t1] = xi;
+  if (L::D == 3)
+    X[t2] = xj;
+  else
+    X[2] = 0;
+  // each boundary node is written by the first face (lowest axis) holding it
+  for (int b = 0; b < a; ++b)
+    if (J.boxed[b] && (X[b] == 0 || X[b] == c.n[b] - 1)) return;
+  // eq. spaceInt weights: -1/16 on the outer, 9/16 on the inner points
+  auto sw = [](int k) { return (k == 0 || k == 3) ? -1.0f / 16.0f : 9.0f / 16.0f; };
+  const bool oi = xi & 1, oj = (L::D == 3) && (xj & 1);
+  const int ni = oi ? 4 : 1, nj = oj ? 4 : 1;
+  // window index of the stencil's first point along each tangent axis
+  const int bi = (oi ? (xi - 3) / 2 : xi / 2) - p0i;
+  const int bj = (L::D == 3) ? ((oj ? (xj - 3) / 2 : xj / 2) - p0j) : 0;
+  float acc[T::NV];
+#pragma unroll
+  for (int j = 0; j < T::NV; ++j) acc[j] = 0.0f;
+  for (int sj = 0; sj < nj; ++sj)
+    for (int si = 0; si < ni; ++si) {
+      const float w = (oi ? sw(si) : 1.0f) * (oj ? sw(sj) : 1.0f);
+#pragma unroll
+      for (int j = 0; j < T::NV; ++j) acc[j] += w * sv[j][bj + sj][bi + si];
+    }
   float g[L::Q];
-  equilibrium<L>(acc[0], rho0 + acc[0], acc[1], acc[2], acc[3], g);
+  equilibrium_f<L>(acc[0], acc[1], acc[2], acc[3], ref, g);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     g[i] += resc * acc[4 + i];
   });
-  S* f = static_cast<S*>(c.f) + run * c.run_stride;
-  const NodeAddr a = node_addr<L>(c, X[0], X[1], X[2]);
-  store_pre<L, S>(f, c.plane, a, par, g);
+  S* fb = static_cast<S*>(c.f) + run * c.run_stride;
+  const NodeAddr ad = node_addr<L>(c, X[0], X[1], X[2]);
+  store_pre<L, S>(fb, c.plane, ad, par, g);
 }
 
 // ----------------------------------------------------------- K4: restrict
 // Parent TN nodes.  resc = 2 tau_c / tau_f (eq. rescfc); ppar / cpar: the
-// parent's and the child's next updates.
+// parent's and the child's next updates.  A block handles kTnPerBlock TN
+// nodes with one thread per (TN node, filter neighbour): each thread forms
+// the weighted f^(1) of its child node, the block sums the 3^D neighbours in
+// a fixed order (so results do not depend on scheduling), and one thread per
+// TN node rebuilds and stores the populations.
+template <class L>
+struct TnShape {
+  static constexpr int NB = (L::D == 3) ? 27 : 9;   // filter neighbours
+  static constexpr int M = (L::D == 3) ? 8 : 16;    // TN nodes per block
+};
+
 template <class L, class S>
-__global__ void k_restrict(LevelView p, LevelView c, TnDesc T, float resc, int ppar, int cpar,
-                           float rho0) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
+    k_restrict(LevelView p, LevelView c, TnDesc T, float resc, int ppar, int cpar, RefF ref) {
+  constexpr int NB = TnShape<L>::NB, M = TnShape<L>::M, Q = L::Q;
+  __shared__ float red[M][NB][Q];
+  __shared__ float cm[M][4];
+  const int kn = threadIdx.x, m = threadIdx.y;
+  const long long k = (long long)blockIdx.x * M + m;
   const int run = blockIdx.y;
-  if (k >= T.count) return;
-  const int fc = ring_face(T.start, T.nf, k);
-  long long loc = k - T.start[fc];
-  int P[3], X[3];
+  const bool valid = k < T.count;
+  int P[3] = {0, 0, 0}, X[3] = {0, 0, 0};
+  if (valid) {
+    const int fc = ring_face(T.start, T.nf, k);
+    long long loc = k - T.start[fc];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int e = T.rext[fc][a];
-    const int r = T.rlo[fc][a] + (int)(loc % e);
-    loc /= e;
-    if (T.boxed[a]) {
-      int pc = T.lo[a] + r;
-      if (p.per[a]) pc = wrapi(pc, p.n[a]);
-      P[a] = pc;
-      X[a] = 2 * r;
-    } else {
-      P[a] = r;
+    for (int a = 0; a < 3; ++a) {
+      const int e = T.rext[fc][a];
+      const int r = T.rlo[fc][a] + (int)(loc % e);
+      loc /= e;
+      if (T.boxed[a]) {
+        int pc = T.lo[a] + r;
+        if (p.per[a]) pc = wrapi(pc, p.n[a]);
+        P[a] = pc;
+      } else {
+        P[a] = r;
+      }
       X[a] = 2 * r;
     }
-  }
-  const S* fc_ = static_cast<const S*>(c.f) + run * c.run_stride;
-  float f1s[L::Q];
+    const int dx = kn % 3 - 1, dy = (kn / 3) % 3 - 1, dz = (L::D == 3) ? kn / 9 - 1 : 0;
+    int xx = X[0] + dx, yy = X[1] + dy, zz = X[2] + dz;
+    if (c.per[0]) xx = wrapi(xx, c.n[0]);
+    if (c.per[1]) yy = wrapi(yy, c.n[1]);
+    if (L::D == 3 && c.per[2]) zz = wrapi(zz, c.n[2]);
+    const S* fcb = static_cast<const S*>(c.f) + run * c.run_stride;
+    const NodeAddr a = node_addr<L>(c, xx, yy, zz);
+    float g[Q], f1[Q], drho, ux, uy, uz;  // (ux, uy, uz): velocity deviations
+    load_pre<L, S>(fcb, c.plane, a, cpar, g);
+    split_neq<L>(g, ref, drho, ux, uy, uz, f1);
+    const float w = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) *
+                    (L::D == 3 ? (dz == 0 ? 0.5f : 0.25f) : 1.0f);
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) f1s[i] = 0.0f;
-  float drho_c = 0.0f, ux_c = 0.0f, uy_c = 0.0f, uz_c = 0.0f;
-  const int dzr = (L::D == 3) ? 1 : 0;
-  for (int dz = -dzr; dz <= dzr; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        int xx = X[0] + dx, yy = X[1] + dy, zz = X[2] + dz;
-        if (c.per[0]) xx = wrapi(xx, c.n[0]);
-        if (c.per[1]) yy = wrapi(yy, c.n[1]);
-        if (L::D == 3 && c.per[2]) zz = wrapi(zz, c.n[2]);
-        const NodeAddr a = node_addr<L>(c, xx, yy, zz);
-        float g[L::Q], f1[L::Q], drho, ux, uy, uz;
-        load_pre<L, S>(fc_, c.plane, a, cpar, g);
-        split_neq<L>(g, rho0, drho, ux, uy, uz, f1);
-        const float w = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) *
-                        (L::D == 3 ? (dz == 0 ? 0.5f : 0.25f) : 1.0f);
-        sfor<L::Q>([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          f1s[i] += w * f1[i];
-        });
-        if (dx == 0 && dy == 0 && dz == 0) {
-          drho_c = drho;
-          ux_c = ux;
-          uy_c = uy;
-          uz_c = uz;
-        }
-      }
-  float g[L::Q];
-  equilibrium<L>(drho_c, rho0 + drho_c, ux_c, uy_c, uz_c, g);
-  sfor<L::Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    g[i] += resc * f1s[i];
-  });
-  S* fp = static_cast<S*>(p.f) + run * p.run_stride;
-  const NodeAddr a = node_addr<L>(p, P[0], P[1], P[2]);
-  store_pre<L, S>(fp, p.plane, a, ppar, g);
+    for (int i = 0; i < Q; ++i) red[m][kn][i] = w * f1[i];
+    if (dx == 0 && dy == 0 && dz == 0) {
+      cm[m][0] = drho;
+      cm[m][1] = ux;
+      cm[m][2] = uy;
+      cm[m][3] = uz;
+    }
+  }
+  __syncthreads();
+  // fixed-order sum over the neighbours, one thread per population
+  if (valid && kn < Q) {
+    float s = 0.0f;
+    for (int n = 0; n < NB; ++n) s += red[m][n][kn];
+    red[m][0][kn] = s;  // row 0 was read by this thread only, first
+  }
+  __syncthreads();
+  if (valid && kn == 0) {
+    float g[Q];
+    equilibrium_f<L>(cm[m][0], cm[m][1], cm[m][2], cm[m][3], ref, g);
+    sfor<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      g[i] += resc * red[m][0][i];
+    });
+    S* fp = static_cast<S*>(p.f) + run * p.run_stride;
+    const NodeAddr a = node_addr<L>(p, P[0], P[1], P[2]);
+    store_pre<L, S>(fp, p.plane, a, ppar, g);
+  }
 }
 
 // ------------------------------------------------------ set-up / read-out
@@ -374,16 +471,18 @@ __device__ __forceinline__ bool node_of(const LevelView& v, long long t, int& x,
 }
 
 // Equilibrium initial state from FP64 fields, laid out as after a parity-0
-// update (post-collision g_i at plane opp(i) of the node).
+// update (post-collision g_i at plane opp(i) of the node), in FP64 up to the
+// final rounding to the storage type.
 template <class L, class S>
-__global__ void k_init(LevelView v, int run, const double* rho, const double* u, double rho0) {
+__global__ void k_init(LevelView v, int run, const double* rho, const double* u, RefState ref) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
   const long long N = (long long)v.n[0] * v.n[1] * v.n[2];
   const double r = rho[t];
   double g0[L::Q];
-  equilibrium<L, double>(r - rho0, r, u[t], u[N + t], u[2 * N + t], g0);
+  equilibrium_dev<L, double>(r - ref.rho0, u[t] - ref.U[0], u[N + t] - ref.U[1],
+                             u[2 * N + t] - ref.U[2], ref.rho0, ref.U[0], ref.U[1], ref.U[2], g0);
   S* f = static_cast<S*>(v.f) + run * v.run_stride;
   const NodeAddr a = node_addr<L>(v, x, y, z);
   sfor<L::Q>([&](auto I) {
@@ -395,7 +494,7 @@ __global__ void k_init(LevelView v, int run, const double* rho, const double* u,
 // rho and u (FP64 or FP32 outputs) of the post-collision state; NaN at
 // inactive nodes.
 template <class L, class S, class T>
-__global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, double rho0) {
+__global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, RefState ref) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
@@ -412,16 +511,18 @@ __global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, double rh
   load_post<L, S>(f, v.plane, a, last, g);
   float drho, jx, jy, jz;
   moments<L>(g, drho, jx, jy, jz);
-  const double r = rho0 + (double)drho;
+  // rho u = sum xi g + rho0 U
+  const double r = ref.rho0 + (double)drho;
   rho[t] = T(r);
-  u[t] = T((double)jx / r);
-  u[N + t] = T((double)jy / r);
-  u[2 * N + t] = T(L::D == 3 ? (double)jz / r : 0.0);
+  u[t] = T(((double)jx + ref.rho0 * ref.U[0]) / r);
+  u[N + t] = T(((double)jy + ref.rho0 * ref.U[1]) / r);
+  u[2 * N + t] = T(L::D == 3 ? ((double)jz + ref.rho0 * ref.U[2]) / r : 0.0);
 }
 
-// Shifted populations of the post-collision state, [q][N] FP64.
+// Post-collision populations shifted by the rest state, f_i - w_i rho0,
+// [q][N] FP64 (the stored deviations plus f0_i(rho0, U) - w_i rho0).
 template <class L, class S>
-__global__ void k_populations(LevelView v, int run, int last, double* out) {
+__global__ void k_populations(LevelView v, int run, int last, double* out, RefState ref) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
@@ -430,15 +531,17 @@ __global__ void k_populations(LevelView v, int run, int last, double* out) {
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
   load_post<L, S>(f, v.plane, a, last, g);
+  double base[L::Q];
+  equilibrium_dev<L, double>(0.0, ref.U[0], ref.U[1], ref.U[2], ref.rho0, 0.0, 0.0, 0.0, base);
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) out[(long long)i * N + t] = (double)g[i];
+  for (int i = 0; i < L::Q; ++i) out[(long long)i * N + t] = (double)g[i] + base[i];
 }
 
 // FP64 per-block partial sums of (drho, rho u) over active nodes; a fixed
 // shared-memory tree order makes the result deterministic.
 template <class L, class S>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(LevelView v, int run, int last,
-                                                               double* partial) {
+                                                               double* partial, RefState ref) {
   __shared__ double sh[4][kDiagThreads];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double s[4] = {0, 0, 0, 0};
@@ -456,6 +559,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(LevelView v, int 
       s[2] += L::c(i, 1) * gi;
       s[3] += L::c(i, 2) * gi;
     });
+    for (int a = 0; a < 3; ++a) s[1 + a] += ref.rho0 * ref.U[a];
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] = s[j];
@@ -476,7 +580,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(LevelView v, int 
 // the counter after all threads have read it.
 template <class L, class S>
 __global__ void k_probe(LevelView v, int last, const int* ijk, int n, double* rec, int cap,
-                        unsigned long long* counter, double rho0) {
+                        unsigned long long* counter, RefState ref) {
   __shared__ unsigned long long slot;
   if (threadIdx.x == 0) slot = *counter;
   __syncthreads();
@@ -489,12 +593,12 @@ __global__ void k_probe(LevelView v, int last, const int* ijk, int n, double* re
     load_post<L, S>(f, v.plane, a, last, g);
     float drho, jx, jy, jz;
     moments<L>(g, drho, jx, jy, jz);
-    const double r = rho0 + (double)drho;
+    const double r = ref.rho0 + (double)drho;
     double* o = rec + (base + (long long)run * n + k) * 4;
     o[0] = r;
-    o[1] = jx / r;
-    o[2] = jy / r;
-    o[3] = (L::D == 3) ? jz / r : 0.0;
+    o[1] = ((double)jx + ref.rho0 * ref.U[0]) / r;
+    o[2] = ((double)jy + ref.rho0 * ref.U[1]) / r;
+    o[3] = (L::D == 3) ? ((double)jz + ref.rho0 * ref.U[2]) / r : 0.0;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = slot + 1;

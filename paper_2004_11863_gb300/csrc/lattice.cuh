@@ -1,6 +1,11 @@
 // Velocity sets and the Hermite-equilibrium / collision arithmetic of the
 // level update, evaluated in binary32 on shifted populations
-// g_i = f_i - w_i rho0.
+// g_i = f_i - f0_i(rho0, U): deviations from the equilibrium of a reference
+// state (rho0, U).  With U = 0 this is the rest-state shift f_i - w_i rho0;
+// a reference velocity near the flow's mean velocity keeps the stored values
+// (and every rounding of them) small where the flow is close to it.  All
+// arithmetic below is written in the deviations drho = rho - rho0 and
+// du = u - U, so that no large terms cancel.
 //
 // Lattices: D2Q9 in the velocity order of Sec. 3.1 (eqs. xi_i, w_i); D3Q19
 // and D3Q27 built the same way (weights 1/3, 1/18, 1/36 and 8/27, 2/27, 1/54,
@@ -126,6 +131,21 @@ __host__ __device__ __forceinline__ T third(const T (&A)[7]) {
   }
 }
 
+// w_i * x without a systematic bias: binary32 cannot hold 1/9, 1/36, ...
+// exactly, and a rounded weight would shift the equilibrium's mass and
+// momentum by the same relative amount at every update (a drift that adds up
+// over long runs).  The weight is split into a binary32 head and tail.
+template <class L, int I, class T>
+__host__ __device__ __forceinline__ T wmul(T x) {
+  if constexpr (std::is_same<T, float>::value) {
+    constexpr float hi = float(L::w(I));
+    constexpr float lo = float(L::w(I) - double(hi));
+    return fmaf(hi, x, lo * x);
+  } else {
+    return T(L::w(I)) * x;
+  }
+}
+
 // xi_i . v with compile-time components.
 template <class L, int I, class T>
 __host__ __device__ __forceinline__ T cdot(T vx, T vy, T vz) {
@@ -158,12 +178,11 @@ __host__ __device__ __forceinline__ void moments(const T (&g)[L::Q], T& drho, T&
   });
 }
 
-// Shifted equilibrium g0_i = f0_i(rho0 + drho, u) - w_i rho0.
-template <class L, class T>
-__host__ __device__ __forceinline__ void equilibrium(T drho, T rho, T ux, T uy, T uz,
-                                                     T (&g0)[L::Q]) {
-  if constexpr (L::D == 2) uz = T(0);
-  T A[7];
+// Third-order coefficients of u (A) and their deviations from those of U
+// (dA = A(u) - A(U)), in the order [xxy, xxz, yyx, yyz, zzx, zzy, xyz].
+template <class T>
+__host__ __device__ __forceinline__ void third_coeffs(T ux, T uy, T uz, T dux, T duy, T duz,
+                                                      T Ux, T Uy, T Uz, T (&A)[7], T (&dA)[7]) {
   A[XXY] = ux * ux * uy;
   A[XXZ] = ux * ux * uz;
   A[YYX] = uy * uy * ux;
@@ -171,34 +190,142 @@ __host__ __device__ __forceinline__ void equilibrium(T drho, T rho, T ux, T uy, 
   A[ZZX] = uz * uz * ux;
   A[ZZY] = uz * uz * uy;
   A[XYZ] = ux * uy * uz;
+  // a^2 b - A^2 B = da (a + A) b + A^2 db
+  dA[XXY] = dux * (ux + Ux) * uy + Ux * Ux * duy;
+  dA[XXZ] = dux * (ux + Ux) * uz + Ux * Ux * duz;
+  dA[YYX] = duy * (uy + Uy) * ux + Uy * Uy * dux;
+  dA[YYZ] = duy * (uy + Uy) * uz + Uy * Uy * duz;
+  dA[ZZX] = duz * (uz + Uz) * ux + Uz * Uz * dux;
+  dA[ZZY] = duz * (uz + Uz) * uy + Uz * Uz * duy;
+  dA[XYZ] = dux * uy * uz + Ux * (duy * uz + Uy * duz);
+}
+
+// Equilibrium deviation for direction I:
+//   g0_i = f0_i(rho0 + drho, U + du) - f0_i(rho0, U)
+//        = w_i [ drho (1 + e_i(u)) + rho0 (e_i(u) - e_i(U)) ],
+//   e_i(u) = 3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u + T3_i(u u u),
+//   e_i(u) - e_i(U) = 3 xi.du + 4.5 (xi.du)(xi.u + xi.U) - 1.5 du.(u + U) + T3_i(dA).
+template <class L, int I, class T>
+__host__ __device__ __forceinline__ T eq_dev_i(T drho, T rho0, T ux, T uy, T uz, T dux, T duy,
+                                               T duz, T Ux, T Uy, T Uz, T usq, T dusq,
+                                               const T (&A)[7], const T (&dA)[7]) {
+  const T cu = cdot<L, I>(ux, uy, uz);
+  const T cdu = cdot<L, I>(dux, duy, duz);
+  const T cU = cdot<L, I>(Ux, Uy, Uz);
+  const T e = T(3) * cu + T(4.5) * cu * cu - usq + third<L, I>(A);
+  const T de = T(3) * cdu + T(4.5) * cdu * (cu + cU) - dusq + third<L, I>(dA);
+  return wmul<L, I>(drho * (T(1) + e) + rho0 * de);
+}
+
+// All q equilibrium deviations at (rho0 + drho, U + du).
+template <class L, class T>
+__host__ __device__ __forceinline__ void equilibrium_dev(T drho, T dux, T duy, T duz, T rho0,
+                                                         T Ux, T Uy, T Uz, T (&g0)[L::Q]) {
+  if constexpr (L::D == 2) {
+    duz = T(0);
+    Uz = T(0);
+  }
+  const T ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
+  T A[7], dA[7];
+  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, A, dA);
   const T usq = T(1.5) * (ux * ux + uy * uy + uz * uz);
+  const T dusq = T(1.5) * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    const T cu = cdot<L, i>(ux, uy, uz);
-    const T e = T(3) * cu + T(4.5) * cu * cu - usq + third<L, i>(A);
-    g0[i] = T(L::w(i)) * (drho + rho * e);
+    g0[i] = eq_dev_i<L, i>(drho, rho0, ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, usq, dusq, A, dA);
   });
 }
 
-// In-place collision of shifted populations g -> post-collision state.
+// Reference state (rho0, U) of the shifted storage, in binary32, with the
+// per-direction constants the equilibrium deviation needs:
+// c1[i] = 1 + e_i(U) and cU2[i] = 2 xi_i.U (formed once on the host).
+struct RefF {
+  float rho0, Ux, Uy, Uz;
+  float c1[27];
+  float cU2[27];
+};
+
+// Equilibrium deviation of direction I from the deviations alone:
+//   g0_i = w_i [ drho (1 + e_i(U)) + (rho0 + drho) (e_i(u) - e_i(U)) ],
+//   e_i(u) - e_i(U) = 3 xi.du + 4.5 (xi.du)(2 xi.U + xi.du) - dusq + T3_i(dA),
+// with dusq = 1.5 du.(2U + du) and dA the deviations of the third-order
+// coefficients (third_coeffs).  MOV = false folds U = 0: c1 = 1, cU2 = 0,
+// and the expression is the rest-state equilibrium w_i [drho + rho e_i(u)].
+template <class L, int I, bool MOV>
+__device__ __forceinline__ float eq_i(float drho, float rho, float dux, float duy, float duz,
+                                      float dusq, const float (&dA)[7], const RefF& R) {
+  const float cdu = cdot<L, I>(dux, duy, duz);
+  const float cu2 = MOV ? R.cU2[I] : 0.0f;
+  const float c1 = MOV ? R.c1[I] : 1.0f;
+  const float de = 3.0f * cdu + 4.5f * cdu * (cu2 + cdu) - dusq + third<L, I>(dA);
+  return wmul<L, I>(drho * c1 + rho * de);
+}
+
+// All q equilibrium deviations (binary32) at (rho0 + drho, U + du).
+template <class L>
+__device__ __forceinline__ void equilibrium_f(float drho, float dux, float duy, float duz,
+                                              const RefF& R, float (&g0)[L::Q]) {
+  const float Ux = R.Ux, Uy = R.Uy, Uz = (L::D == 3) ? R.Uz : 0.0f;
+  if constexpr (L::D == 2) duz = 0.0f;
+  const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
+  float A[7], dA[7];
+  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, A, dA);
+  const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
+  const float rho = R.rho0 + drho;
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    g0[i] = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, R);
+  });
+}
+
+// Density and velocity deviations of shifted populations:
+// drho = sum g, du = (sum xi g - drho U) / (rho0 + drho).
+template <class L>
+__device__ __forceinline__ void deviations(const float (&g)[L::Q], const RefF& R, float& drho,
+                                           float& dux, float& duy, float& duz) {
+  float jx, jy, jz;
+  moments<L>(g, drho, jx, jy, jz);
+  const float inv = 1.0f / (R.rho0 + drho);
+  dux = (jx - drho * R.Ux) * inv;
+  duy = (jy - drho * R.Uy) * inv;
+  duz = (L::D == 3) ? (jz - drho * R.Uz) * inv : 0.0f;
+}
+
+// Collision of shifted populations; the post-collision value of each
+// direction is handed to emit(integral_constant<i>, value) as soon as it is
+// formed, so no array of outputs (or of equilibria) stays live.
 // COLL: 0 BGK (eq. BGKmodel), 1 REG (eq. LBMscheme_reg with H^(2) only),
 // 2 RR (eqs. f1RR, a13RR).  omega = 1 - 1/tau.
-template <class L, int COLL>
-__device__ __forceinline__ void collide(float (&g)[L::Q], float omega, float rho0) {
+// MOV = false: the reference velocity is zero (rest-state shift) and every
+// term in U is folded away at compile time.
+template <class L, int COLL, bool MOV, class Emit>
+__device__ __forceinline__ void collide_emit(const float (&g)[L::Q], float omega, const RefF& Rin,
+                                             Emit&& emit) {
+  // (moments, deviations and the equilibrium of each direction)
+  const float Ux = MOV ? Rin.Ux : 0.0f, Uy = MOV ? Rin.Uy : 0.0f,
+              Uz = (MOV && L::D == 3) ? Rin.Uz : 0.0f, rho0 = Rin.rho0;
   float drho, jx, jy, jz;
   moments<L>(g, drho, jx, jy, jz);
   const float rho = rho0 + drho;
   const float inv = 1.0f / rho;
-  const float ux = jx * inv, uy = jy * inv, uz = (L::D == 3) ? jz * inv : 0.0f;
-  float g0[L::Q];
-  equilibrium<L>(drho, rho, ux, uy, uz, g0);
+  const float dux = (jx - drho * Ux) * inv, duy = (jy - drho * Uy) * inv,
+              duz = (L::D == 3) ? (jz - drho * Uz) * inv : 0.0f;
+  const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
+  float Ae[7], dAe[7];
+  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, Ae, dAe);
+  const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
+  auto g0_of = [&](auto I) {
+    constexpr int i = decltype(I)::value;
+    return eq_i<L, i, MOV>(drho, rho, dux, duy, duz, dusq, dAe, Rin);
+  };
   if constexpr (COLL == 0) {
     sfor<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      g[i] = g0[i] + omega * (g[i] - g0[i]);
+      const float g0 = g0_of(I);
+      emit(I, g0 + omega * (g[i] - g0));
     });
   } else {
-    // shifted second moments
+    // second moments of the deviations g
     float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
     sfor<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -213,13 +340,25 @@ __device__ __forceinline__ void collide(float (&g)[L::Q], float omega, float rho
       if constexpr (cy * cz == 1) pyz += g[i];
       if constexpr (cy * cz == -1) pyz -= g[i];
     });
+    // a1 = sum xi xi g - drho cs^2 I - drho u u - rho0 (u u - U U),
+    // with u_a u_b - U_a U_b = du_a u_b + U_a du_b
     const float dc = drho * (1.0f / 3.0f);
-    const float axx = pxx - rho * ux * ux - dc;
-    const float ayy = pyy - rho * uy * uy - dc;
-    const float azz = (L::D == 3) ? pzz - rho * uz * uz - dc : 0.0f;
-    const float axy = pxy - rho * ux * uy;
-    const float axz = (L::D == 3) ? pxz - rho * ux * uz : 0.0f;
-    const float ayz = (L::D == 3) ? pyz - rho * uy * uz : 0.0f;
+    float axx, ayy, azz, axy, axz, ayz;
+    if constexpr (MOV) {
+      axx = pxx - dc - drho * ux * ux - rho0 * dux * (ux + Ux);
+      ayy = pyy - dc - drho * uy * uy - rho0 * duy * (uy + Uy);
+      azz = (L::D == 3) ? pzz - dc - drho * uz * uz - rho0 * duz * (uz + Uz) : 0.0f;
+      axy = pxy - drho * ux * uy - rho0 * (dux * uy + Ux * duy);
+      axz = (L::D == 3) ? pxz - drho * ux * uz - rho0 * (dux * uz + Ux * duz) : 0.0f;
+      ayz = (L::D == 3) ? pyz - drho * uy * uz - rho0 * (duy * uz + Uy * duz) : 0.0f;
+    } else {  // U = 0
+      axx = pxx - rho * ux * ux - dc;
+      ayy = pyy - rho * uy * uy - dc;
+      azz = (L::D == 3) ? pzz - rho * uz * uz - dc : 0.0f;
+      axy = pxy - rho * ux * uy;
+      axz = (L::D == 3) ? pxz - rho * ux * uz : 0.0f;
+      ayz = (L::D == 3) ? pyz - rho * uy * uz : 0.0f;
+    }
     float A[7] = {0, 0, 0, 0, 0, 0, 0};
     if constexpr (COLL == 2) {
       A[XXY] = 2.0f * ux * axy + uy * axx;
@@ -236,18 +375,18 @@ __device__ __forceinline__ void collide(float (&g)[L::Q], float omega, float rho
       constexpr int i = decltype(I)::value;
       constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
       // 4.5 * H2_i : a1, with H2_aa = xi_a^2 - 1/3 and both off-diagonal terms
-      constexpr float dxx = 4.5f * (float(cx * cx) - 1.0f / 3.0f);
-      constexpr float dyy = 4.5f * (float(cy * cy) - 1.0f / 3.0f);
+      constexpr float dxx = float(4.5 * (double(cx * cx) - 1.0 / 3.0));
+      constexpr float dyy = float(4.5 * (double(cy * cy) - 1.0 / 3.0));
       constexpr float oxy = 9.0f * float(cx * cy);
       float h2a = dxx * axx + dyy * ayy + oxy * axy;
       if constexpr (L::D == 3) {
-        constexpr float dzz = 4.5f * (float(cz * cz) - 1.0f / 3.0f);
+        constexpr float dzz = float(4.5 * (double(cz * cz) - 1.0 / 3.0));
         constexpr float oxz = 9.0f * float(cx * cz), oyz = 9.0f * float(cy * cz);
         h2a += dzz * azz + oxz * axz + oyz * ayz;
       }
       float f1 = h2a;
       if constexpr (COLL == 2) f1 += third<L, i>(A);
-      g[i] = g0[i] + omega * (float(L::w(i)) * f1);
+      emit(I, g0_of(I) + omega * wmul<L, i>(f1));
     });
   }
 }
@@ -258,12 +397,16 @@ struct Store;
 template <>
 struct Store<float> {
   __device__ __forceinline__ static float ld(const float* p) { return *p; }
+  __device__ __forceinline__ static float ldg(const float* p) { return __ldg(p); }
   __device__ __forceinline__ static void st(float* p, float v) { *p = v; }
+  __device__ __forceinline__ static void stcs(float* p, float v) { __stcs(p, v); }
 };
 template <>
 struct Store<__half> {
   __device__ __forceinline__ static float ld(const __half* p) { return __half2float(*p); }
+  __device__ __forceinline__ static float ldg(const __half* p) { return __half2float(__ldg(p)); }
   __device__ __forceinline__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+  __device__ __forceinline__ static void stcs(__half* p, float v) { __stcs(p, __float2half_rn(v)); }
 };
 
 }  // namespace mlbm

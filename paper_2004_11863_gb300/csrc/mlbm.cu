@@ -63,6 +63,7 @@ struct Level {
   BndDesc bnd{};
   TnDesc tn{};  // TN nodes of the parent
   void* hist_mem = nullptr;
+  int head = 1;  // history slot holding the newest parent state (t+1)
 };
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -71,11 +72,16 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct lbm_ctx {
   lbm_config cfg{};
+  RefState ref{};  // reference state of the shifted storage
   int q = 0, D = 0, nlev = 0, batch = 1;
   Ops ops{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cur = nullptr;
+  // side stream per level: a parent's update runs there, beside its child's
+  // second sub-step (they touch disjoint memory)
+  cudaStream_t side[LBM_MAX_LEVELS] = {};
+  cudaEvent_t ev_fork[LBM_MAX_LEVELS] = {}, ev_join[LBM_MAX_LEVELS] = {};
   bool has_alloc = false;
   lbm_allocator alloc{};
   Level lev[LBM_MAX_LEVELS];
@@ -84,8 +90,11 @@ struct lbm_ctx {
   bool seeded = false;
   long long coarse_steps = 0;
   bool use_graphs = true;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  long long exec_nodes[2] = {0, 0};
+  // One graph per phase of a coarse step: level-0 parity (period 2) times
+  // the history-slot rotation of every interface (period 3).
+  static constexpr int kPhases = 6;
+  cudaGraphExec_t exec[kPhases] = {};
+  long long exec_nodes[kPhases] = {};
   long long launches = 0;
   // per-kernel CUDA-event timing (lbm_profile)
   struct Rec {
@@ -140,7 +149,7 @@ Ops ops_for(int lattice) {
 }
 
 void drop_graphs(lbm_ctx* h) {
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < lbm_ctx::kPhases; ++k)
     if (h->exec[k]) {
       cudaGraphExecDestroy(h->exec[k]);
       h->exec[k] = nullptr;
@@ -160,6 +169,11 @@ void release(lbm_ctx* h) {
   h->dfree(h->probe_rec);
   h->dfree(h->probe_counter);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int l = 0; l < LBM_MAX_LEVELS; ++l) {
+    if (h->side[l]) cudaStreamDestroy(h->side[l]);
+    if (h->ev_fork[l]) cudaEventDestroy(h->ev_fork[l]);
+    if (h->ev_join[l]) cudaEventDestroy(h->ev_join[l]);
+  }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   h->event_pool.clear();
 }
@@ -376,24 +390,46 @@ inline float omega_of(double tau) { return (float)(1.0 - 1.0 / tau); }
 int advance(lbm_ctx* h, int l, const float* wt, bool launch) {
   Level& v = h->lev[l];
   const int st = h->cfg.storage;
-  const float rho0 = (float)h->cfg.rho0;
+  const RefState& ref = h->ref;
   const int par = 1 - v.last;
   if (l >= 1) {
     const Level& p = h->lev[l - 1];
     const float resc = (float)(v.tau / (2.0 * p.tau));  // eq. rescff
-    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, resc, par, rho0, h->cur));
+    const int slots[3] = {(v.head + 1) % 3, (v.head + 2) % 3, v.head};  // t-1, t, t+1
+    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref, h->cur));
   }
   if (l + 1 < h->nlev) {
     Level& c = h->lev[l + 1];
-    LAUNCH_K(1, l, h->ops.capture(v.view, c.ring, st, par, 0, rho0, h->cur));
+    c.head = (c.head + 1) % 3;
+    LAUNCH_K(1, l, h->ops.capture(v.view, c.ring, st, par, 0, c.head, c.head, ref, h->cur));
     int rc = advance(h, l + 1, v.nsteps == 0 ? kTimeLin : kTimeQuad, launch);
     if (rc) return rc;
     const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
-    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, rho0, h->cur));
+    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref, h->cur));
+    // Level l's own update needs nothing the child's second sub-step
+    // produces and touches none of its memory: run it on the side stream
+    // (serialised while profiling, so each kernel is timed alone).
+    cudaStream_t main = h->cur;
+    const bool fork = launch && !h->profiling;
+    if (fork) {
+      CK(cudaEventRecord(h->ev_fork[l], main));
+      CK(cudaStreamWaitEvent(h->side[l], h->ev_fork[l], 0));
+      h->cur = h->side[l];
+    }
+    LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
+                                         h->cur));
+    if (fork) {
+      CK(cudaEventRecord(h->ev_join[l], h->side[l]));
+      h->cur = main;
+    }
+    v.last = par;
+    v.nsteps++;
     rc = advance(h, l + 1, kTimeDirect, launch);
     if (rc) return rc;
+    if (fork) CK(cudaStreamWaitEvent(main, h->ev_join[l], 0));
+    return LBM_OK;
   }
-  LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), rho0, h->cur));
+  LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref, h->cur));
   v.last = par;
   v.nsteps++;
   return LBM_OK;
@@ -403,7 +439,7 @@ int probe_launch(lbm_ctx* h, bool launch) {
   if (h->probe_n <= 0) return LBM_OK;
   const Level& v = h->lev[h->probe_level];
   LAUNCH_K(4, h->probe_level, h->ops.probe(v.view, h->cfg.storage, v.last, h->probe_ijk, h->probe_n, h->probe_rec,
-                      h->probe_cap, h->probe_counter, h->cfg.rho0, h->cur));
+                      h->probe_cap, h->probe_counter, h->ref, h->cur));
   return LBM_OK;
 }
 
@@ -413,13 +449,15 @@ int coarse_step(lbm_ctx* h, bool launch) {
   return probe_launch(h, launch);
 }
 
-// History set-up after initialisation: slots t and t+1 <- (drho, u, 0).
+// History set-up after initialisation: slots 0 (t) and 1 (t+1, the
+// newest) <- (drho, u, 0) of the initial state.
 int seed_history(lbm_ctx* h) {
   const bool launch = true;
   h->cur = h->stream;
   for (int l = 1; l < h->nlev; ++l) {
     Level& p = h->lev[l - 1];
-    LAUNCH(h->ops.capture(p.view, h->lev[l].ring, h->cfg.storage, p.last, 1, (float)h->cfg.rho0,
+    h->lev[l].head = 1;
+    LAUNCH(h->ops.capture(p.view, h->lev[l].ring, h->cfg.storage, p.last, 1, 1, 0, h->ref,
                           h->cur));
   }
   h->seeded = true;
@@ -471,10 +509,15 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
       cfg->nlevels > LBM_MAX_LEVELS || cfg->batch < 1 || !(cfg->tau0 > 0.5) ||
       !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau0))
     return LBM_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(cfg->u_ref[a]) || std::fabs(cfg->u_ref[a]) > 0.5) return LBM_EINVAL;
+  if (cfg->lattice == LBM_D2Q9 && cfg->u_ref[2] != 0.0) return LBM_EINVAL;
   if (alloc && (!alloc->alloc || !alloc->free)) return LBM_EINVAL;
   lbm_ctx* h = new (std::nothrow) lbm_ctx();
   if (!h) return LBM_ENOMEM;
   h->cfg = *cfg;
+  h->ref.rho0 = cfg->rho0;
+  for (int a = 0; a < 3; ++a) h->ref.U[a] = cfg->u_ref[a];
   h->ops = ops_for(cfg->lattice);
   h->q = h->ops.q;
   h->D = h->ops.d;
@@ -499,7 +542,13 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
       return LBM_EINVAL;
     }
   }
-  for (int l = 0; l < h->nlev; ++l) build_view(h, l);
+  for (int l = 0; l < h->nlev; ++l) {
+    build_view(h, l);
+    if (h->lev[l].view.plane > 2147483647LL) {  // kernels index planes in 32 bits
+      delete h;
+      return LBM_EINVAL;
+    }
+  }
   for (int l = 1; l < h->nlev; ++l) build_interface(h, l);
   // device memory
   for (int l = 0; l < h->nlev; ++l) {
@@ -528,7 +577,12 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
       cudaMemsetAsync(v.hist_mem, 0, hb, h->stream);
     }
   }
-  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (int l = 0; l < h->nlev && ok; ++l)
+    ok = cudaStreamCreateWithFlags(&h->side[l], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_fork[l], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     release(h);
     delete h;
     return LBM_ECUDA;
@@ -572,7 +626,7 @@ int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* 
       rc = LBM_ECUDA;
       break;
     }
-    cudaError_t e = h->ops.init(v.view, h->cfg.storage, run, d, d + N, h->cfg.rho0, h->stream);
+    cudaError_t e = h->ops.init(v.view, h->cfg.storage, run, d, d + N, h->ref, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
       snprintf(g_errmsg, sizeof(g_errmsg), "init: %s", cudaGetErrorString(e));
@@ -614,7 +668,9 @@ int lbm_step(lbm_handle h, int n_coarse) {
       int rc = coarse_step(h, true);
       if (rc) return rc;
     } else {
-      const int key = 1 - h->lev[0].last;
+      // every level's parity and every history rotation restart with the
+      // initial state, so the phase of a coarse step is its index mod 6
+      const int key = (int)(h->coarse_steps % lbm_ctx::kPhases);
       if (!h->exec[key]) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -655,7 +711,7 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
   const long long N = v.n_nodes;
   double* d = (double*)h->dalloc(sizeof(double) * 4 * N);
   if (!d) return LBM_ENOMEM;
-  cudaError_t e = h->ops.macros_d(v.view, h->cfg.storage, run, v.last, d, d + N, h->cfg.rho0,
+  cudaError_t e = h->ops.macros_d(v.view, h->cfg.storage, run, v.last, d, d + N, h->ref,
                                   h->stream);
   ++h->launches;
   if (e == cudaSuccess)
@@ -676,8 +732,7 @@ int lbm_macros_device(lbm_handle h, int level, int run, float* rho_dev, float* u
     return LBM_EINVAL;
   if (!h->ready) return LBM_ESTATE;
   const Level& v = h->lev[level];
-  CK(h->ops.macros_f(v.view, h->cfg.storage, run, v.last, rho_dev, u_dev, h->cfg.rho0,
-                     h->stream));
+  CK(h->ops.macros_f(v.view, h->cfg.storage, run, v.last, rho_dev, u_dev, h->ref, h->stream));
   ++h->launches;
   return LBM_OK;
 }
@@ -690,7 +745,7 @@ int lbm_populations(lbm_handle h, int level, int run, double* g) {
   const size_t bytes = sizeof(double) * h->q * (size_t)v.n_nodes;
   double* d = (double*)h->dalloc(bytes);
   if (!d) return LBM_ENOMEM;
-  cudaError_t e = h->ops.populations(v.view, h->cfg.storage, run, v.last, d, h->stream);
+  cudaError_t e = h->ops.populations(v.view, h->cfg.storage, run, v.last, d, h->ref, h->stream);
   ++h->launches;
   if (e == cudaSuccess) e = cudaMemcpyAsync(g, d, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -766,7 +821,8 @@ int lbm_diag(lbm_handle h, int run, double* mass, double* mom) {
     double* part = (double*)h->dalloc(sizeof(double) * 4 * nb);
     if (!part) return LBM_ENOMEM;
     std::vector<double> hp((size_t)4 * nb);
-    cudaError_t e = h->ops.diag_partial(v.view, h->cfg.storage, run, v.last, part, nb, h->stream);
+    cudaError_t e =
+        h->ops.diag_partial(v.view, h->cfg.storage, run, v.last, part, nb, h->ref, h->stream);
     ++h->launches;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost,
@@ -901,7 +957,7 @@ extern "C" int lbm_diag_noalloc(lbm_handle h, int run, double* mass, double* mom
     const int nb = (int)((v.n_nodes + kDiagThreads - 1) / kDiagThreads);
     // every partial the final sum reads is written first, so nothing needs
     // clearing between calls
-    CK(h->ops.diag_partial(v.view, h->cfg.storage, run, v.last, partial, nb, h->stream));
+    CK(h->ops.diag_partial(v.view, h->cfg.storage, run, v.last, partial, nb, h->ref, h->stream));
     k_diag_final<<<1, 32, 0, h->stream>>>(partial, nb, result);
     CK(cudaGetLastError());
     h->launches += 2;

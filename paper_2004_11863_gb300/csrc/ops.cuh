@@ -13,28 +13,29 @@ struct Ops {
   int q, d;
   // K1: fused stream + collide of every active node of a level.
   cudaError_t (*stream_collide)(const LevelView& v, int coll, int storage, int par, float omega,
-                                float rho0, cudaStream_t s);
+                                const RefState& ref, cudaStream_t s);
   // K2: history capture (mode 0) or set-up (mode 1).
   cudaError_t (*capture)(const LevelView& p, const RingDesc& R, int storage, int par, int mode,
-                         float rho0, cudaStream_t s);
+                         int s_new, int s_also, const RefState& ref, cudaStream_t s);
   // K3: coarse -> fine boundary rebuild.
   cudaError_t (*inject)(const LevelView& c, const BndDesc& B, const RingDesc& R, int storage,
-                        const float* wt, float resc, int par, float rho0, cudaStream_t s);
+                        const float* wt, const int* slots, float resc, int par, const RefState& ref,
+                        cudaStream_t s);
   // K4: fine -> coarse restriction.
   cudaError_t (*restrict_tn)(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
-                             float resc, int ppar, int cpar, float rho0, cudaStream_t s);
+                             float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s);
   cudaError_t (*init)(const LevelView& v, int storage, int run, const double* rho, const double* u,
-                      double rho0, cudaStream_t s);
+                      const RefState& ref, cudaStream_t s);
   cudaError_t (*macros_d)(const LevelView& v, int storage, int run, int last, double* rho,
-                          double* u, double rho0, cudaStream_t s);
+                          double* u, const RefState& ref, cudaStream_t s);
   cudaError_t (*macros_f)(const LevelView& v, int storage, int run, int last, float* rho, float* u,
-                          double rho0, cudaStream_t s);
+                          const RefState& ref, cudaStream_t s);
   cudaError_t (*populations)(const LevelView& v, int storage, int run, int last, double* out,
-                             cudaStream_t s);
+                             const RefState& ref, cudaStream_t s);
   cudaError_t (*diag_partial)(const LevelView& v, int storage, int run, int last, double* partial,
-                              int nblocks, cudaStream_t s);
+                              int nblocks, const RefState& ref, cudaStream_t s);
   cudaError_t (*probe)(const LevelView& v, int storage, int last, const int* ijk, int n,
-                       double* rec, int cap, unsigned long long* counter, double rho0,
+                       double* rec, int cap, unsigned long long* counter, const RefState& ref,
                        cudaStream_t s);
 };
 

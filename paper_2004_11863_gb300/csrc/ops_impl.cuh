@@ -9,67 +9,123 @@ namespace detail {
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// binary32 reference state with the per-direction constants 1 + e_i(U) and
+// 2 xi_i.U, formed in double precision.
+template <class L>
+RefF make_ref_f(const RefState& r) {
+  RefF R{};
+  R.rho0 = (float)r.rho0;
+  R.Ux = (float)r.U[0];
+  R.Uy = (float)r.U[1];
+  R.Uz = L::D == 3 ? (float)r.U[2] : 0.0f;
+  const double Uz = L::D == 3 ? r.U[2] : 0.0;
+  double eU[L::Q];
+  // e_i(U) = (f0_i(1, U) - w_i) / w_i
+  double f0[L::Q];
+  equilibrium_dev<L, double>(0.0, r.U[0], r.U[1], Uz, 1.0, 0.0, 0.0, 0.0, f0);
+  for (int i = 0; i < L::Q; ++i) {
+    eU[i] = f0[i] / L::w(i);
+    R.c1[i] = (float)(1.0 + eU[i]);
+    R.cU2[i] = (float)(2.0 * (L::c(i, 0) * r.U[0] + L::c(i, 1) * r.U[1] + L::c(i, 2) * Uz));
+  }
+  return R;
+}
+
 template <class L, class S, int COLL>
-cudaError_t sc_launch(const LevelView& v, int par, float omega, float rho0, cudaStream_t s) {
+cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, cudaStream_t s) {
   dim3 block(32, 4, 1);
   dim3 grid((v.n[0] + 31) / 32, (v.n[1] + 3) / 4, v.n[2] * v.batch);
-  if (par == 0)
-    k_stream_collide<L, COLL, S, 0><<<grid, block, 0, s>>>(v, omega, rho0);
-  else
-    k_stream_collide<L, COLL, S, 1><<<grid, block, 0, s>>>(v, omega, rho0);
+  const bool mov = ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
+  const RefF R = make_ref_f<L>(ref);
+  if (mov) {
+    if (par == 0)
+      k_stream_collide<L, COLL, S, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+    else
+      k_stream_collide<L, COLL, S, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+  } else {
+    if (par == 0)
+      k_stream_collide<L, COLL, S, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+    else
+      k_stream_collide<L, COLL, S, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+  }
   return cudaGetLastError();
 }
 
 template <class L, class S>
-cudaError_t sc_coll(const LevelView& v, int coll, int par, float omega, float rho0,
+cudaError_t sc_coll(const LevelView& v, int coll, int par, float omega, const RefState& ref,
                     cudaStream_t s) {
   switch (coll) {
-    case 0: return sc_launch<L, S, 0>(v, par, omega, rho0, s);
-    case 1: return sc_launch<L, S, 1>(v, par, omega, rho0, s);
-    default: return sc_launch<L, S, 2>(v, par, omega, rho0, s);
+    case 0: return sc_launch<L, S, 0>(v, par, omega, ref, s);
+    case 1: return sc_launch<L, S, 1>(v, par, omega, ref, s);
+    default: return sc_launch<L, S, 2>(v, par, omega, ref, s);
   }
 }
 
 template <class L>
 cudaError_t stream_collide(const LevelView& v, int coll, int storage, int par, float omega,
-                           float rho0, cudaStream_t s) {
-  return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, rho0, s)
-                      : sc_coll<L, __half>(v, coll, par, omega, rho0, s);
+                           const RefState& ref, cudaStream_t s) {
+  return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, ref, s)
+                      : sc_coll<L, __half>(v, coll, par, omega, ref, s);
 }
 
 template <class L>
 cudaError_t capture(const LevelView& p, const RingDesc& R, int storage, int par, int mode,
-                    float rho0, cudaStream_t s) {
+                    int s_new, int s_also, const RefState& ref, cudaStream_t s) {
   if (R.K == 0) return cudaSuccess;
   dim3 grid(blocks_for(R.K, 128), p.batch);
   if (storage == 0)
-    k_capture<L, float><<<grid, 128, 0, s>>>(p, R, par, mode, rho0);
+    k_capture<L, float><<<grid, 128, 0, s>>>(p, R, par, mode, s_new, s_also, make_ref_f<L>(ref));
   else
-    k_capture<L, __half><<<grid, 128, 0, s>>>(p, R, par, mode, rho0);
+    k_capture<L, __half><<<grid, 128, 0, s>>>(p, R, par, mode, s_new, s_also, make_ref_f<L>(ref));
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t inject(const LevelView& c, const BndDesc& B, const RingDesc& R, int storage,
-                   const float* wt, float resc, int par, float rho0, cudaStream_t s) {
+                   const float* wt, const int* slots, float resc, int par, const RefState& ref,
+                   cudaStream_t s) {
   if (B.count == 0) return cudaSuccess;
-  dim3 grid(blocks_for(B.count, 128), c.batch);
+  using T = InjTile<L>;
+  InjDesc J{};
+  J.nf = B.nf;
+  J.tstart[0] = 0;
+  for (int a = 0; a < 3; ++a) J.boxed[a] = R.boxed[a];
+  for (int f = 0; f < B.nf; ++f) {
+    const int a = B.axis[f];
+    J.axis[f] = a;
+    J.side[f] = B.side[f];
+    if (L::D == 2) {
+      J.t1[f] = 1 - a;
+      J.t2[f] = 2;
+    } else {
+      J.t1[f] = (a == 0) ? 1 : 0;
+      J.t2[f] = (a == 2) ? 1 : 2;
+    }
+    J.ntile1[f] = (c.n[J.t1[f]] + T::TI - 1) / T::TI;
+    J.ntile2[f] = (L::D == 3) ? (c.n[J.t2[f]] + T::TJ - 1) / T::TJ : 1;
+    J.tstart[f + 1] = J.tstart[f] + (long long)J.ntile1[f] * J.ntile2[f];
+  }
+  dim3 grid((unsigned)J.tstart[J.nf], c.batch);
+  dim3 block(T::TI, T::TJ);
   if (storage == 0)
-    k_inject<L, float><<<grid, 128, 0, s>>>(c, B, R, wt[0], wt[1], wt[2], resc, par, rho0);
+    k_inject<L, float><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0], slots[1],
+                                              slots[2], resc, par, make_ref_f<L>(ref));
   else
-    k_inject<L, __half><<<grid, 128, 0, s>>>(c, B, R, wt[0], wt[1], wt[2], resc, par, rho0);
+    k_inject<L, __half><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0], slots[1],
+                                               slots[2], resc, par, make_ref_f<L>(ref));
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t restrict_tn(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
-                        float resc, int ppar, int cpar, float rho0, cudaStream_t s) {
+                        float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s) {
   if (T.count == 0) return cudaSuccess;
-  dim3 grid(blocks_for(T.count, 64), p.batch);
+  dim3 block(TnShape<L>::NB, TnShape<L>::M);
+  dim3 grid(blocks_for(T.count, TnShape<L>::M), p.batch);
   if (storage == 0)
-    k_restrict<L, float><<<grid, 64, 0, s>>>(p, c, T, resc, ppar, cpar, rho0);
+    k_restrict<L, float><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, make_ref_f<L>(ref));
   else
-    k_restrict<L, __half><<<grid, 64, 0, s>>>(p, c, T, resc, ppar, cpar, rho0);
+    k_restrict<L, __half><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, make_ref_f<L>(ref));
   return cudaGetLastError();
 }
 
@@ -77,65 +133,65 @@ inline long long nodes(const LevelView& v) { return (long long)v.n[0] * v.n[1] *
 
 template <class L>
 cudaError_t init(const LevelView& v, int storage, int run, const double* rho, const double* u,
-                 double rho0, cudaStream_t s) {
+                 const RefState& ref, cudaStream_t s) {
   unsigned g = blocks_for(nodes(v), 128);
   if (storage == 0)
-    k_init<L, float><<<g, 128, 0, s>>>(v, run, rho, u, rho0);
+    k_init<L, float><<<g, 128, 0, s>>>(v, run, rho, u, ref);
   else
-    k_init<L, __half><<<g, 128, 0, s>>>(v, run, rho, u, rho0);
+    k_init<L, __half><<<g, 128, 0, s>>>(v, run, rho, u, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t macros_d(const LevelView& v, int storage, int run, int last, double* rho, double* u,
-                     double rho0, cudaStream_t s) {
+                     const RefState& ref, cudaStream_t s) {
   unsigned g = blocks_for(nodes(v), 128);
   if (storage == 0)
-    k_macros<L, float, double><<<g, 128, 0, s>>>(v, run, last, rho, u, rho0);
+    k_macros<L, float, double><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
   else
-    k_macros<L, __half, double><<<g, 128, 0, s>>>(v, run, last, rho, u, rho0);
+    k_macros<L, __half, double><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t macros_f(const LevelView& v, int storage, int run, int last, float* rho, float* u,
-                     double rho0, cudaStream_t s) {
+                     const RefState& ref, cudaStream_t s) {
   unsigned g = blocks_for(nodes(v), 128);
   if (storage == 0)
-    k_macros<L, float, float><<<g, 128, 0, s>>>(v, run, last, rho, u, rho0);
+    k_macros<L, float, float><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
   else
-    k_macros<L, __half, float><<<g, 128, 0, s>>>(v, run, last, rho, u, rho0);
+    k_macros<L, __half, float><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t populations(const LevelView& v, int storage, int run, int last, double* out,
-                        cudaStream_t s) {
+                        const RefState& ref, cudaStream_t s) {
   unsigned g = blocks_for(nodes(v), 128);
   if (storage == 0)
-    k_populations<L, float><<<g, 128, 0, s>>>(v, run, last, out);
+    k_populations<L, float><<<g, 128, 0, s>>>(v, run, last, out, ref);
   else
-    k_populations<L, __half><<<g, 128, 0, s>>>(v, run, last, out);
+    k_populations<L, __half><<<g, 128, 0, s>>>(v, run, last, out, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t diag_partial(const LevelView& v, int storage, int run, int last, double* partial,
-                         int nblocks, cudaStream_t s) {
+                         int nblocks, const RefState& ref, cudaStream_t s) {
   if (storage == 0)
-    k_diag_partial<L, float><<<nblocks, kDiagThreads, 0, s>>>(v, run, last, partial);
+    k_diag_partial<L, float><<<nblocks, kDiagThreads, 0, s>>>(v, run, last, partial, ref);
   else
-    k_diag_partial<L, __half><<<nblocks, kDiagThreads, 0, s>>>(v, run, last, partial);
+    k_diag_partial<L, __half><<<nblocks, kDiagThreads, 0, s>>>(v, run, last, partial, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t probe(const LevelView& v, int storage, int last, const int* ijk, int n, double* rec,
-                  int cap, unsigned long long* counter, double rho0, cudaStream_t s) {
+                  int cap, unsigned long long* counter, const RefState& ref, cudaStream_t s) {
   if (storage == 0)
-    k_probe<L, float><<<1, 256, 0, s>>>(v, last, ijk, n, rec, cap, counter, rho0);
+    k_probe<L, float><<<1, 256, 0, s>>>(v, last, ijk, n, rec, cap, counter, ref);
   else
-    k_probe<L, __half><<<1, 256, 0, s>>>(v, last, ijk, n, rec, cap, counter, rho0);
+    k_probe<L, __half><<<1, 256, 0, s>>>(v, last, ijk, n, rec, cap, counter, ref);
   return cudaGetLastError();
 }
 

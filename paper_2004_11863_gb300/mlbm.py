@@ -40,7 +40,8 @@ class lbm_config(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("collision", ctypes.c_int), ("storage", ctypes.c_int),
                 ("tau0", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("dims", ctypes.c_int * 3), ("nlevels", ctypes.c_int),
-                ("box", lbm_box * (MAX_LEVELS - 1)), ("batch", ctypes.c_int)]
+                ("box", lbm_box * (MAX_LEVELS - 1)), ("batch", ctypes.c_int),
+                ("u_ref", ctypes.c_double * 3)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -115,7 +116,8 @@ def lbm_lattice(lattice: str):
 
 
 def make_config(lattice: str, collision: str, tau0: float, dims: Sequence[int], boxes,
-                storage: str = "fp32", batch: int = 1, rho0: float = 1.0) -> lbm_config:
+                storage: str = "fp32", batch: int = 1, rho0: float = 1.0,
+                u_ref=(0.0, 0.0, 0.0)) -> lbm_config:
     c = lbm_config()
     c.lattice = workloads.LATTICES[lattice]
     c.collision = workloads.COLLISIONS[collision]
@@ -131,6 +133,8 @@ def make_config(lattice: str, collision: str, tau0: float, dims: Sequence[int], 
             c.box[k].lo[a] = int(lo[a])
             c.box[k].hi[a] = int(hi[a])
     c.batch = int(batch)
+    for a in range(3):
+        c.u_ref[a] = float(u_ref[a])
     return c
 
 
@@ -163,9 +167,9 @@ class Lbm:
     """
 
     def __init__(self, lattice, collision, tau0, dims, boxes, storage="fp32", batch=1,
-                 rho0=1.0, stream=None, torch_allocator=False):
+                 rho0=1.0, stream=None, torch_allocator=False, u_ref=(0.0, 0.0, 0.0)):
         L = lib()
-        self.cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0)
+        self.cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0, u_ref)
         self.lattice = lattice
         self.q = workloads.Q_OF[lattice]
         self.nlevels = self.cfg.nlevels
@@ -182,6 +186,7 @@ class Lbm:
 
     @classmethod
     def from_case(cls, case, storage="fp32", batch=1, init=True, **kw):
+        kw.setdefault("u_ref", case.u_ref)
         r = cls(case.lattice, case.collision, case.tau0, case.dims, case.boxes, storage, batch,
                 case.rho0, **kw)
         if init:

@@ -48,6 +48,12 @@ class Case:
     rho0: float = 1.0
 
     @property
+    def u_ref(self):
+        """Reference velocity for the shifted storage: the mean (free-stream)
+        velocity of the initial condition."""
+        return tuple(float(v) for v in self.ic.get("u0", (0.0, 0.0, 0.0)))
+
+    @property
     def dim(self) -> int:
         return DIM_OF[self.lattice]
 

@@ -84,6 +84,36 @@ def test_parity_3d(M, name, mk):
     compare(g, o, case.nlevels)
 
 
+@pytest.mark.parametrize("u_ref", [(0.0, 0.0, 0.0), (0.1 * W.CS, 0.0, 0.0), (0.03, -0.02, 0.0)])
+def test_reference_shift_does_not_change_results(M, u_ref):
+    """The stored shift f - f0(rho0, U) is a storage choice: any reference
+    velocity gives the oracle's result within the binary32 tolerance."""
+    case = W.vortex_2level_d2q9(steps=60)
+    g = M.Lbm.from_case(case, u_ref=u_ref)
+    o = oracle.Run.from_case(case)
+    g.step(case.steps)
+    o.step(case.steps)
+    compare(g, o, 2)
+
+
+def test_populations_are_rest_shifted(M):
+    """lbm_populations returns f - w rho0 whatever the reference velocity;
+    matched to the oracle's populations direction by direction."""
+    case = W.small_3d("D3Q19", "RR", nlevels=2, steps=3)
+    g = M.Lbm.from_case(case, u_ref=(0.04, 0.01, -0.02))
+    o = oracle.Run.from_case(case)
+    g.step(3)
+    o.step(3)
+    xg, _ = M.lbm_lattice("D3Q19")
+    xo, wo = oracle.lattice("D3Q19")
+    order = [int(np.nonzero((xo == v).all(1))[0][0]) for v in xg]
+    for l in range(2):
+        pg = g.populations(l)
+        po = o.populations(l) - wo[:, None] * case.rho0
+        m = ~np.isnan(o.macros(l)[0])
+        np.testing.assert_allclose(pg[:, m], po[order][:, m], rtol=0, atol=1e-6)
+
+
 def test_three_level_2d(M):
     case = W.Case("nest2d", "D2Q9", "RR", 0.51, (64, 64, 1),
                   [((16, 16, 0), (48, 48, 1)), ((16, 16, 0), (48, 48, 1))],
@@ -126,13 +156,13 @@ def test_batch_runs_independent(M):
     bit for bit."""
     c1 = W.small_2level_2d("RR")
     c2 = c1.with_(ic=dict(kind="pulse", center=(50.0, 20.0, 0.0), radius=3.0, amplitude=2e-3))
-    g = M.Lbm(c1.lattice, c1.collision, c1.tau0, c1.dims, c1.boxes, batch=2)
+    g = M.Lbm(c1.lattice, c1.collision, c1.tau0, c1.dims, c1.boxes, batch=2, u_ref=c1.u_ref)
     for l in range(2):
         g.init(l, 0, *W.initial_fields(c1, l))
         g.init(l, 1, *W.initial_fields(c2, l))
     g.step(7)
     for run, c in ((0, c1), (1, c2)):
-        s = M.Lbm.from_case(c)
+        s = M.Lbm.from_case(c, u_ref=c1.u_ref)
         s.step(7)
         for l in range(2):
             r1, u1 = g.macros(l, run)
