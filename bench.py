@@ -41,7 +41,13 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the kernel
 # sources it was taken on; ignored once the sources change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the fine-level
+    # update of the 33-run benchmark (parity 1: 331.6 + 262.2 MB; parity 0:
+    # 331.6 + 255.0 MB); stored per run so that any batch scales it.
+    ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 590.1e6 / 33,
+                                       "src": "b284b0d61cd8aacd"},
+}
 
 
 def kernel_source_hash() -> str:
@@ -294,7 +300,8 @@ def main():
     peak, peak_kind = measured_peaks()
     src_hash = kernel_source_hash()
     tr = NCU_TRAFFIC.get((args.workload, args.storage, dom))
-    traffic = tr["bytes_per_launch_scaled"] * batch if tr and tr["src"] == src_hash else None
+    traffic = (round(tr["bytes_per_launch_per_run"] * batch)
+               if tr and tr["src"] == src_hash else None)
     step_total = sum(v[0] for v in kt.values()) / args.steps
     shares = {k: round(v[0] / args.steps / step_total, 4) for k, v in kt.items()}
 

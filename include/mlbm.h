@@ -140,6 +140,32 @@ int lbm_level_info(lbm_handle h, int level, int* n, double* tau,
 int lbm_init(lbm_handle h, int level, int run, const double* rho,
              const double* u);
 
+/* Analytic initial states, evaluated in FP64 on the device at every node of
+ * every level (node positions in level-0 units, periodic minimum image):
+ *   LBM_IC_UNIFORM: rho = rho0 + drho, u = u0;
+ *   LBM_IC_VORTEX:  convected vortex of Sec. 10.1 (eq. init_COVO) about the
+ *                   z axis through center, with the linearised density
+ *                   rho0 [1 - eps^2/(2 cs^2) exp(-r^2/R^2)] and
+ *                   u = u0 + eps (-(y-yc), x-xc)/R exp(-r^2/(2R^2));
+ *   LBM_IC_PULSE:   Gaussian density pulse of Sec. 9.2 (eq. init_Pulse),
+ *                   rho = rho0 [1 + amplitude exp(-r^2/(2R^2))], u = u0. */
+#define LBM_IC_UNIFORM 0
+#define LBM_IC_VORTEX 1
+#define LBM_IC_PULSE 2
+typedef struct {
+  int kind;
+  double u0[3];
+  double center[3];
+  double radius;    /* R */
+  double amplitude; /* pulse amplitude A */
+  double eps;       /* vortex strength */
+  double drho;      /* uniform density offset */
+} lbm_ic;
+
+/* Set every level of one run to the equilibrium of an analytic state
+ * (same rules as lbm_init, without host arrays).  Synchronises. */
+int lbm_init_analytic(lbm_handle h, int run, const lbm_ic* ic);
+
 /* Advance every run by n_coarse level-0 steps (level l takes 2^l sub-steps
  * each, Sec. 4.3).  Asynchronous.  The first step after lbm_init starts the
  * coarse-to-fine temporal interpolation with the linear rule; later steps
@@ -203,6 +229,17 @@ int lbm_diag(lbm_handle h, int run, double* mass, double* mom);
  * array needs clearing, because every call writes each value before reading
  * it.  Synchronises. */
 int lbm_diag_noalloc(lbm_handle h, int run, double* mass, double* mom);
+
+/* Spurious-noise diagnostic: the density difference between a refined run
+ * and the same initial state on the uniform level-0 grid alone (a second
+ * handle, `single`, with the same level-0 layout, lattice and storage),
+ * over level-0 nodes outside the refined run's level-1 box by at least
+ * `margin` cells on every bounded axis, where the refined solution should
+ * only differ by what the interface emits.  Reduced in FP64 on the device:
+ * *max_abs = max |rho_refined - rho_single|, *rms = root mean square,
+ * *count = nodes used (may be NULL).  Synchronises both handles. */
+int lbm_noise(lbm_handle refined, lbm_handle single, int run, int margin,
+              double* max_abs, double* rms, long long* count);
 
 /* Block until all work issued by the handle has finished. */
 int lbm_sync(lbm_handle h);

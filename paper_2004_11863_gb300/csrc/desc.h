@@ -34,6 +34,25 @@ struct RefState {
   double U[3];
 };
 
+// Analytic initial state evaluated on the device (kinds as in mlbm.h).
+struct ICDesc {
+  int kind;  // 0 uniform, 1 vortex (about z), 2 Gaussian pulse
+  double u0[3], center[3], radius, amplitude, eps, drho;
+};
+
+// Node positions of a level in level-0 units: origin + h * index, wrapped
+// into the periodic level-0 domain of size dom.
+struct Placement {
+  double origin[3], h;
+  int dom[3];
+};
+
+// Region of level-0 nodes the noise diagnostic skips: nodes within `margin`
+// cells of the child box (box-relative coordinates on bounded axes).
+struct NoiseRegion {
+  int boxed[3], lo[3], E[3], n[3], margin;
+};
+
 constexpr int kMaxFaces = 6;
 
 // Threads per block of the FP64 diagnostic reduction.

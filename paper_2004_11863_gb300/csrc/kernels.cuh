@@ -118,81 +118,197 @@ __device__ __forceinline__ void load_post(const S* f, long long plane, const Nod
 
 // ------------------------------------------------------- K1: level update
 // One thread per node; a warp covers 32 consecutive x of one row.
-// Resident blocks per SM the level update is compiled for: the register
-// budget each lattice's collision fits (D2Q9 40, D3Q19 80, D3Q27 96
-// registers per thread; with a moving reference 48, 96, 128).
-template <class L>
-struct K1Occupancy;
-template <>
-struct K1Occupancy<D2Q9> {
-  static constexpr int MINB_MOV = 10;
-#ifdef K1_MINB_D2Q9
-  static constexpr int MINB = K1_MINB_D2Q9;
-#else
-  static constexpr int MINB = 12;
+// Launch shape of the level update per lattice and storage type: NPT nodes
+// per thread (consecutive rows, so a thread keeps NPT x q loads in flight)
+// and the resident blocks per SM its register budget is compiled for
+// (MINB; MINB_EVEN for the even step, whose accesses share one address;
+// MINB_MOV with a moving reference, whose deviation terms need more
+// registers).  Chosen by measurement (the shape sweep in the benchmarks).
+template <class L, class S>
+struct K1Tune;
+// (each value may be overridden at compile time, e.g. -DK1_NPT_D2Q9_F=1)
+#ifndef K1_NPT_D2Q9_F
+#define K1_NPT_D2Q9_F 1
 #endif
+#ifndef K1_MINB_D2Q9_F
+#define K1_MINB_D2Q9_F 12
+#endif
+#ifndef K1_MINBE_D2Q9_F
+#define K1_MINBE_D2Q9_F K1_MINB_D2Q9_F
+#endif
+#ifndef K1_MINBM_D2Q9_F
+#define K1_MINBM_D2Q9_F 10
+#endif
+#ifndef K1_NPT_D2Q9_H
+#define K1_NPT_D2Q9_H 2
+#endif
+#ifndef K1_MINB_D2Q9_H
+#define K1_MINB_D2Q9_H 6
+#endif
+#ifndef K1_MINBE_D2Q9_H
+#define K1_MINBE_D2Q9_H K1_MINB_D2Q9_H
+#endif
+#ifndef K1_MINBM_D2Q9_H
+#define K1_MINBM_D2Q9_H 6
+#endif
+#ifndef K1_NPT_D3Q19_F
+#define K1_NPT_D3Q19_F 1
+#endif
+#ifndef K1_MINB_D3Q19_F
+#define K1_MINB_D3Q19_F 6
+#endif
+#ifndef K1_MINBE_D3Q19_F
+#define K1_MINBE_D3Q19_F 7
+#endif
+#ifndef K1_MINBM_D3Q19_F
+#define K1_MINBM_D3Q19_F 5
+#endif
+#ifndef K1_NPT_D3Q19_H
+#define K1_NPT_D3Q19_H 1
+#endif
+#ifndef K1_MINB_D3Q19_H
+#define K1_MINB_D3Q19_H 6
+#endif
+#ifndef K1_MINBE_D3Q19_H
+#define K1_MINBE_D3Q19_H K1_MINB_D3Q19_H
+#endif
+#ifndef K1_MINBM_D3Q19_H
+#define K1_MINBM_D3Q19_H 5
+#endif
+#ifndef K1_NPT_D3Q27_F
+#define K1_NPT_D3Q27_F 1
+#endif
+#ifndef K1_MINB_D3Q27_F
+#define K1_MINB_D3Q27_F 5
+#endif
+#ifndef K1_MINBE_D3Q27_F
+#define K1_MINBE_D3Q27_F 6
+#endif
+#ifndef K1_MINBM_D3Q27_F
+#define K1_MINBM_D3Q27_F 4
+#endif
+#ifndef K1_NPT_D3Q27_H
+#define K1_NPT_D3Q27_H 1
+#endif
+#ifndef K1_MINB_D3Q27_H
+#define K1_MINB_D3Q27_H 5
+#endif
+#ifndef K1_MINBE_D3Q27_H
+#define K1_MINBE_D3Q27_H K1_MINB_D3Q27_H
+#endif
+#ifndef K1_MINBM_D3Q27_H
+#define K1_MINBM_D3Q27_H 4
+#endif
+template <>
+struct K1Tune<D2Q9, float> {
+  static constexpr int NPT = K1_NPT_D2Q9_F, MINB = K1_MINB_D2Q9_F,
+                       MINB_EVEN = K1_MINBE_D2Q9_F, MINB_MOV = K1_MINBM_D2Q9_F;
 };
 template <>
-struct K1Occupancy<D3Q19> {
-  static constexpr int MINB_MOV = 5;
-#ifdef K1_MINB_D3Q19
-  static constexpr int MINB = K1_MINB_D3Q19;
-#else
-  static constexpr int MINB = 6;
-#endif
+struct K1Tune<D2Q9, __half> {
+  static constexpr int NPT = K1_NPT_D2Q9_H, MINB = K1_MINB_D2Q9_H,
+                       MINB_EVEN = K1_MINBE_D2Q9_H, MINB_MOV = K1_MINBM_D2Q9_H;
 };
 template <>
-struct K1Occupancy<D3Q27> {
-  static constexpr int MINB_MOV = 4;
-#ifdef K1_MINB_D3Q27
-  static constexpr int MINB = K1_MINB_D3Q27;
-#else
-  static constexpr int MINB = 5;
-#endif
+struct K1Tune<D3Q19, float> {
+  static constexpr int NPT = K1_NPT_D3Q19_F, MINB = K1_MINB_D3Q19_F,
+                       MINB_EVEN = K1_MINBE_D3Q19_F, MINB_MOV = K1_MINBM_D3Q19_F;
 };
-// MOV: the storage is shifted by a moving reference (u_ref != 0); its extra
-// deviation terms get a larger register budget (MINB_MOV resident blocks).
+template <>
+struct K1Tune<D3Q19, __half> {
+  static constexpr int NPT = K1_NPT_D3Q19_H, MINB = K1_MINB_D3Q19_H,
+                       MINB_EVEN = K1_MINBE_D3Q19_H, MINB_MOV = K1_MINBM_D3Q19_H;
+};
+template <>
+struct K1Tune<D3Q27, float> {
+  static constexpr int NPT = K1_NPT_D3Q27_F, MINB = K1_MINB_D3Q27_F,
+                       MINB_EVEN = K1_MINBE_D3Q27_F, MINB_MOV = K1_MINBM_D3Q27_F;
+};
+template <>
+struct K1Tune<D3Q27, __half> {
+  static constexpr int NPT = K1_NPT_D3Q27_H, MINB = K1_MINB_D3Q27_H,
+                       MINB_EVEN = K1_MINBE_D3Q27_H, MINB_MOV = K1_MINBM_D3Q27_H;
+};
+
+// Addresses of a strip of NPT consecutive rows (same x and z): node k's
+// neighbour (dx, dy, dz) sits at zo[dz+1] + yo[k+dy+1] + xo[dx+1].
+template <int NPT>
+struct StripAddr {
+  int zo[3];
+  int yo[NPT + 2];
+  int xo[3];
+  __device__ __forceinline__ int at(int k, int dx, int dy, int dz) const {
+    return zo[dz + 1] + yo[k + dy + 1] + xo[dx + 1];
+  }
+};
+
+// One thread updates NPT nodes (x, y0 .. y0+NPT-1, z); a warp covers 32
+// consecutive x of NPT rows.  All loads of the thread's nodes are issued
+// before the first collision.
 template <class L, int COLL, class S, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, MOV ? K1Occupancy<L>::MINB_MOV : K1Occupancy<L>::MINB)
+__global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
+                                           : (PAR == 0 ? K1Tune<L, S>::MINB_EVEN
+                                                       : K1Tune<L, S>::MINB))
     k_stream_collide(LevelView v, float omega, RefF R) {
+  constexpr int NPT = K1Tune<L, S>::NPT;
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int y0 = (blockIdx.y * 4 + threadIdx.y) * NPT;
   int z = blockIdx.z, run = 0;
   if (v.batch > 1) {
     run = z / v.n[2];
     z -= run * v.n[2];
   }
-  if (x >= v.n[0] || y >= v.n[1]) return;
-  if (inactive(v, x, y, z)) return;
+  if (x >= v.n[0] || y0 >= v.n[1]) return;
   S* f = static_cast<S*>(v.f) + run * v.run_stride;
-  const NodeAddr a = node_addr<L>(v, x, y, z);
-  float g[L::Q];
-#ifdef K1_LDG
-  sfor<L::Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    if constexpr (PAR == 0)
-      g[i] = Store<S>::ldg(f + (long long)i * v.plane + a.at(0, 0, 0));
-    else
-      g[i] = Store<S>::ldg(f + (long long)opp<L>(i) * v.plane +
-                           a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
-  });
-#else
-  load_pre<L, S>(f, v.plane, a, PAR, g);
-#endif
-  collide_emit<L, COLL, MOV>(g, omega, R, [&](auto I, float val) {
-    constexpr int i = decltype(I)::value;
-#ifdef K1_STCS
-    if constexpr (PAR == 0)
-      Store<S>::stcs(f + (long long)opp<L>(i) * v.plane + a.at(0, 0, 0), val);
-    else
-      Store<S>::stcs(f + (long long)i * v.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), val);
-#else
-    if constexpr (PAR == 0)
-      Store<S>::st(f + (long long)opp<L>(i) * v.plane + a.at(0, 0, 0), val);
-    else
-      Store<S>::st(f + (long long)i * v.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)), val);
-#endif
-  });
+  StripAddr<NPT> a;
+  const int off = (int)v.off;
+#pragma unroll
+  for (int d = -1; d <= 1; ++d) {
+    int xx = x + d;
+    if (v.per[0]) xx = wrapi(xx, v.n[0]);
+    a.xo[d + 1] = xx + off;
+    if constexpr (L::D == 3) {
+      int zz = z + d;
+      if (v.per[2]) zz = wrapi(zz, v.n[2]);
+      a.zo[d + 1] = zz * v.SY * v.SX;
+    } else {
+      a.zo[d + 1] = 0;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NPT + 2; ++r) {
+    int yy = y0 - 1 + r;
+    if (v.per[1]) yy = wrapi(yy, v.n[1]);
+    a.yo[r] = yy * v.SX;
+  }
+  bool ok[NPT];
+  float g[NPT][L::Q];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    ok[k] = (y0 + k < v.n[1]) && !inactive(v, x, y0 + k, z);
+    if (ok[k]) {
+      sfor<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (PAR == 0)
+          g[k][i] = Store<S>::ld(f + (long long)i * v.plane + a.at(k, 0, 0, 0));
+        else
+          g[k][i] = Store<S>::ld(f + (long long)opp<L>(i) * v.plane +
+                                 a.at(k, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
+      });
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    if (!ok[k]) continue;
+    collide_emit<L, COLL, MOV>(g[k], omega, R, [&](auto I, float val) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (PAR == 0)
+        Store<S>::st(f + (long long)opp<L>(i) * v.plane + a.at(k, 0, 0, 0), val);
+      else
+        Store<S>::st(f + (long long)i * v.plane + a.at(k, L::c(i, 0), L::c(i, 1), L::c(i, 2)),
+                     val);
+    });
+  }
 }
 
 // (drho, du, f^(1)) of a population set (deviations from the reference).
@@ -491,6 +607,62 @@ __global__ void k_init(LevelView v, int run, const double* rho, const double* u,
   });
 }
 
+// FP64 partials of the noise diagnostic: max |drho_a - drho_b| and the sum
+// of squares over level-0 nodes outside the child box by at least
+// `margin` cells (on every bounded axis the node lies outside the box
+// grown by margin), plus the node count.
+template <class L, class S>
+__global__ void __launch_bounds__(kDiagThreads)
+    k_noise_partial(LevelView va, int last_a, RefState ra, LevelView vb, int last_b,
+                    RefState rb, int run, NoiseRegion reg, double* partial) {
+  __shared__ double sh[3][kDiagThreads];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0, ss = 0.0, cnt = 0.0;
+  int x, y, z;
+  if (node_of(va, t, x, y, z)) {
+    const int P[3] = {x, y, z};
+    bool near = true;
+    for (int a = 0; a < 3; ++a) {
+      if (!reg.boxed[a]) continue;
+      int rel = P[a] - reg.lo[a];
+      rel = ((rel % reg.n[a]) + reg.n[a]) % reg.n[a];
+      const bool in_grown = rel <= reg.E[a] + reg.margin || rel >= reg.n[a] - reg.margin;
+      near = near && in_grown;
+    }
+    if (!near) {
+      float ga[L::Q], gb[L::Q];
+      const S* fa = static_cast<const S*>(va.f) + run * va.run_stride;
+      const S* fb = static_cast<const S*>(vb.f) + run * vb.run_stride;
+      load_post<L, S>(fa, va.plane, node_addr<L>(va, x, y, z), last_a, ga);
+      load_post<L, S>(fb, vb.plane, node_addr<L>(vb, x, y, z), last_b, gb);
+      double da = 0.0, db = 0.0;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        da += (double)ga[i];
+        db += (double)gb[i];
+      }
+      const double d = fabs((ra.rho0 + da) - (rb.rho0 + db));
+      mx = d;
+      ss = d * d;
+      cnt = 1.0;
+    }
+  }
+  sh[0][threadIdx.x] = mx;
+  sh[1][threadIdx.x] = ss;
+  sh[2][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + w]);
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 3; ++j) partial[(long long)j * gridDim.x + blockIdx.x] = sh[j][0];
+}
+
 // rho and u (FP64 or FP32 outputs) of the post-collision state; NaN at
 // inactive nodes.
 template <class L, class S, class T>
@@ -509,14 +681,16 @@ __global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, RefState 
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
   load_post<L, S>(f, v.plane, a, last, g);
-  float drho, jx, jy, jz;
-  moments<L>(g, drho, jx, jy, jz);
-  // rho u = sum xi g + rho0 U
-  const double r = ref.rho0 + (double)drho;
+  // moments summed in FP64 (read-out precision): rho u = sum xi g + rho0 U
+  double gd[L::Q], drho, jx, jy, jz;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) gd[i] = (double)g[i];
+  moments<L, double>(gd, drho, jx, jy, jz);
+  const double r = ref.rho0 + drho;
   rho[t] = T(r);
-  u[t] = T(((double)jx + ref.rho0 * ref.U[0]) / r);
-  u[N + t] = T(((double)jy + ref.rho0 * ref.U[1]) / r);
-  u[2 * N + t] = T(L::D == 3 ? ((double)jz + ref.rho0 * ref.U[2]) / r : 0.0);
+  u[t] = T((jx + ref.rho0 * ref.U[0]) / r);
+  u[N + t] = T((jy + ref.rho0 * ref.U[1]) / r);
+  u[2 * N + t] = T(L::D == 3 ? (jz + ref.rho0 * ref.U[2]) / r : 0.0);
 }
 
 // Post-collision populations shifted by the rest state, f_i - w_i rho0,
@@ -591,14 +765,16 @@ __global__ void k_probe(LevelView v, int last, const int* ijk, int n, double* re
     const NodeAddr a = node_addr<L>(v, ijk[3 * k], ijk[3 * k + 1], ijk[3 * k + 2]);
     float g[L::Q];
     load_post<L, S>(f, v.plane, a, last, g);
-    float drho, jx, jy, jz;
-    moments<L>(g, drho, jx, jy, jz);
-    const double r = ref.rho0 + (double)drho;
+    double gd[L::Q], drho, jx, jy, jz;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) gd[i] = (double)g[i];
+    moments<L, double>(gd, drho, jx, jy, jz);
+    const double r = ref.rho0 + drho;
     double* o = rec + (base + (long long)run * n + k) * 4;
     o[0] = r;
-    o[1] = ((double)jx + ref.rho0 * ref.U[0]) / r;
-    o[2] = ((double)jy + ref.rho0 * ref.U[1]) / r;
-    o[3] = (L::D == 3) ? ((double)jz + ref.rho0 * ref.U[2]) / r : 0.0;
+    o[1] = (jx + ref.rho0 * ref.U[0]) / r;
+    o[2] = (jy + ref.rho0 * ref.U[1]) / r;
+    o[3] = (L::D == 3) ? (jz + ref.rho0 * ref.U[2]) / r : 0.0;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = slot + 1;

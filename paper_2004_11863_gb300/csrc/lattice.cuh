@@ -95,6 +95,19 @@ __host__ __device__ constexpr int opp(int i) {
   return k;
 }
 
+// Directions come in opposite pairs (i, opp(i)); pair_first<L>(p) is the
+// lower index of the p-th pair, p = 0 .. (Q-1)/2 - 1.
+template <class L>
+__host__ __device__ constexpr int pair_first(int p) {
+  int k = 0;
+  for (int i = 1; i < L::Q; ++i)
+    if (i < opp<L>(i)) {
+      if (k == p) return i;
+      ++k;
+    }
+  return -1;
+}
+
 // Third-order Hermite polynomial H_aab(xi_i) = xi_a^2 xi_b - cs^2 xi_b.
 template <class L>
 __host__ __device__ constexpr double h3(int i, int a, int b) {
@@ -176,6 +189,50 @@ __host__ __device__ __forceinline__ void moments(const T (&g)[L::Q], T& drho, T&
     if constexpr (L::c(i, 2) == 1) jz += g[i];
     if constexpr (L::c(i, 2) == -1) jz -= g[i];
   });
+}
+
+// Moments from per-axis class sums: S+_a = sum over xi_a = +1, S-_a = sum
+// over xi_a = -1; then j_a = S+_a - S-_a and the diagonal second moment
+// P_aa = S+_a + S-_a, and drho = S+_x + S-_x + (sum over xi_x = 0).  The
+// off-diagonal P_ab sum the four directions with xi_a xi_b = +-1.
+template <class L>
+__device__ __forceinline__ void moments2(const float (&g)[L::Q], float& drho, float (&j)[3],
+                                         float (&pd)[3], float (&po)[3]) {
+  float sp[3] = {0, 0, 0}, sm[3] = {0, 0, 0}, s0 = 0.0f;
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (L::c(i, 0) == 1) sp[0] += g[i];
+    if constexpr (L::c(i, 0) == -1) sm[0] += g[i];
+    if constexpr (L::c(i, 0) == 0) s0 += g[i];
+  });
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (L::c(i, 1) == 1) sp[1] += g[i];
+    if constexpr (L::c(i, 1) == -1) sm[1] += g[i];
+    if constexpr (L::D == 3) {
+      if constexpr (L::c(i, 2) == 1) sp[2] += g[i];
+      if constexpr (L::c(i, 2) == -1) sm[2] += g[i];
+    }
+  });
+  drho = (sp[0] + sm[0]) + s0;
+  for (int a = 0; a < 3; ++a) {
+    j[a] = sp[a] - sm[a];
+    pd[a] = sp[a] + sm[a];
+  }
+  float pxy_p = 0, pxy_m = 0, pxz_p = 0, pxz_m = 0, pyz_p = 0, pyz_m = 0;
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+    if constexpr (cx * cy == 1) pxy_p += g[i];
+    if constexpr (cx * cy == -1) pxy_m += g[i];
+    if constexpr (cx * cz == 1) pxz_p += g[i];
+    if constexpr (cx * cz == -1) pxz_m += g[i];
+    if constexpr (cy * cz == 1) pyz_p += g[i];
+    if constexpr (cy * cz == -1) pyz_m += g[i];
+  });
+  po[0] = pxy_p - pxy_m;
+  po[1] = pxz_p - pxz_m;
+  po[2] = pyz_p - pyz_m;
 }
 
 // Third-order coefficients of u (A) and their deviations from those of U
@@ -304,42 +361,50 @@ __device__ __forceinline__ void collide_emit(const float (&g)[L::Q], float omega
   // (moments, deviations and the equilibrium of each direction)
   const float Ux = MOV ? Rin.Ux : 0.0f, Uy = MOV ? Rin.Uy : 0.0f,
               Uz = (MOV && L::D == 3) ? Rin.Uz : 0.0f, rho0 = Rin.rho0;
-  float drho, jx, jy, jz;
-  moments<L>(g, drho, jx, jy, jz);
+  float drho, jv[3], pd[3], po[3];
+  moments2<L>(g, drho, jv, pd, po);
+  const float jx = jv[0], jy = jv[1], jz = jv[2];
   const float rho = rho0 + drho;
-  const float inv = 1.0f / rho;
+  const float inv = __frcp_rn(rho);  // correctly rounded, as 1.0f / rho
   const float dux = (jx - drho * Ux) * inv, duy = (jy - drho * Uy) * inv,
               duz = (L::D == 3) ? (jz - drho * Uz) * inv : 0.0f;
   const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
   float Ae[7], dAe[7];
   third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, Ae, dAe);
   const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
-  auto g0_of = [&](auto I) {
+  // Opposite directions share the even part of the equilibrium deviation
+  // and of f^(1) and differ in the sign of the odd part:
+  //   de_i = Ev + Od, de_opp(i) = Ev - Od,
+  //   Ev = 4.5 (xi.du)(2 xi.U + xi.du) - dusq,  Od = 3 xi.du + T3_i(dA).
+  // X_i such that g0_i = w_i X_i
+  auto eq_pair = [&](auto I, float& xi, float& xj) {
     constexpr int i = decltype(I)::value;
-    return eq_i<L, i, MOV>(drho, rho, dux, duy, duz, dusq, dAe, Rin);
+    constexpr int j = opp<L>(i);
+    const float cdu = cdot<L, i>(dux, duy, duz);
+    const float cu2 = MOV ? Rin.cU2[i] : 0.0f;
+    const float ev = 4.5f * cdu * (cu2 + cdu) - dusq;
+    const float od = 3.0f * cdu + third<L, i>(dAe);
+    const float c1i = MOV ? Rin.c1[i] : 1.0f, c1j = MOV ? Rin.c1[j] : 1.0f;
+    xi = drho * c1i + rho * (ev + od);
+    xj = drho * c1j + rho * (ev - od);
   };
+  const float x00 = drho * (MOV ? Rin.c1[0] : 1.0f) - rho * dusq;  // rest direction
+  constexpr int NP = (L::Q - 1) / 2;
   if constexpr (COLL == 0) {
-    sfor<L::Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const float g0 = g0_of(I);
-      emit(I, g0 + omega * (g[i] - g0));
+    const float g00 = wmul<L, 0>(x00);
+    emit(std::integral_constant<int, 0>{}, g00 + omega * (g[0] - g00));
+    sfor<NP>([&](auto P) {
+      constexpr int i = pair_first<L>(decltype(P)::value);
+      constexpr int j = opp<L>(i);
+      float xi, xj;
+      eq_pair(std::integral_constant<int, i>{}, xi, xj);
+      const float gi = wmul<L, i>(xi), gj = wmul<L, j>(xj);
+      emit(std::integral_constant<int, i>{}, gi + omega * (g[i] - gi));
+      emit(std::integral_constant<int, j>{}, gj + omega * (g[j] - gj));
     });
   } else {
     // second moments of the deviations g
-    float pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-    sfor<L::Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      if constexpr (cx != 0) pxx += g[i];
-      if constexpr (cy != 0) pyy += g[i];
-      if constexpr (cz != 0) pzz += g[i];
-      if constexpr (cx * cy == 1) pxy += g[i];
-      if constexpr (cx * cy == -1) pxy -= g[i];
-      if constexpr (cx * cz == 1) pxz += g[i];
-      if constexpr (cx * cz == -1) pxz -= g[i];
-      if constexpr (cy * cz == 1) pyz += g[i];
-      if constexpr (cy * cz == -1) pyz -= g[i];
-    });
+    const float pxx = pd[0], pyy = pd[1], pzz = pd[2], pxy = po[0], pxz = po[1], pyz = po[2];
     // a1 = sum xi xi g - drho cs^2 I - drho u u - rho0 (u u - U U),
     // with u_a u_b - U_a U_b = du_a u_b + U_a du_b
     const float dc = drho * (1.0f / 3.0f);
@@ -371,22 +436,34 @@ __device__ __forceinline__ void collide_emit(const float (&g)[L::Q], float omega
         A[XYZ] = ux * ayz + uy * axz + uz * axy;
       }
     }
-    sfor<L::Q>([&](auto I) {
+    // f^(1): 4.5 H2:a1 is even in xi (shared by a pair), T3(a1^(3)) is odd
+    auto h2a_of = [&](auto I) {
       constexpr int i = decltype(I)::value;
       constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      // 4.5 * H2_i : a1, with H2_aa = xi_a^2 - 1/3 and both off-diagonal terms
       constexpr float dxx = float(4.5 * (double(cx * cx) - 1.0 / 3.0));
       constexpr float dyy = float(4.5 * (double(cy * cy) - 1.0 / 3.0));
       constexpr float oxy = 9.0f * float(cx * cy);
-      float h2a = dxx * axx + dyy * ayy + oxy * axy;
+      float h = dxx * axx + dyy * ayy + oxy * axy;
       if constexpr (L::D == 3) {
         constexpr float dzz = float(4.5 * (double(cz * cz) - 1.0 / 3.0));
         constexpr float oxz = 9.0f * float(cx * cz), oyz = 9.0f * float(cy * cz);
-        h2a += dzz * azz + oxz * axz + oyz * ayz;
+        h += dzz * azz + oxz * axz + oyz * ayz;
       }
-      float f1 = h2a;
-      if constexpr (COLL == 2) f1 += third<L, i>(A);
-      emit(I, g0_of(I) + omega * wmul<L, i>(f1));
+      return h;
+    };
+    // post_i = w_i (X_i + omega F_i) with F_i = 4.5 H2_i:a1 + T3_i(a1^(3))
+    emit(std::integral_constant<int, 0>{},
+         wmul<L, 0>(x00 + omega * h2a_of(std::integral_constant<int, 0>{})));
+    sfor<NP>([&](auto P) {
+      constexpr int i = pair_first<L>(decltype(P)::value);
+      constexpr int j = opp<L>(i);
+      float xi, xj;
+      eq_pair(std::integral_constant<int, i>{}, xi, xj);
+      const float h = h2a_of(std::integral_constant<int, i>{});
+      float t = 0.0f;
+      if constexpr (COLL == 2) t = third<L, i>(A);
+      emit(std::integral_constant<int, i>{}, wmul<L, i>(xi + omega * (h + t)));
+      emit(std::integral_constant<int, j>{}, wmul<L, j>(xj + omega * (h - t)));
     });
   }
 }

@@ -63,10 +63,51 @@ struct Level {
   BndDesc bnd{};
   TnDesc tn{};  // TN nodes of the parent
   void* hist_mem = nullptr;
+  double origin[3] = {0, 0, 0}, h = 1.0;  // node positions in level-0 units
   int head = 1;  // history slot holding the newest parent state (t+1)
 };
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Analytic initial fields (FP64) at the nodes of a level, the same
+// definitions as the host-side input generator: uniform flow; convected
+// vortex (Sec. 10.1, linearised density); Gaussian pulse (Sec. 9.2).
+__device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
+
+__global__ void k_ic_fields(LevelView v, Placement pl, ICDesc ic, double rho0, int dim,
+                            double* rho, double* u) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long N = (long long)v.n[0] * v.n[1] * v.n[2];
+  if (t >= N) return;
+  const int x = (int)(t % v.n[0]), y = (int)((t / v.n[0]) % v.n[1]),
+            z = (int)(t / ((long long)v.n[0] * v.n[1]));
+  double X[3] = {pl.origin[0] + pl.h * x, pl.origin[1] + pl.h * y, pl.origin[2] + pl.h * z};
+  for (int a = 0; a < dim; ++a) X[a] = fmod(X[a], (double)pl.dom[a]);
+  double r = rho0, ux = ic.u0[0], uy = ic.u0[1], uz = dim == 3 ? ic.u0[2] : 0.0;
+  const double cs2 = 1.0 / 3.0;
+  if (ic.kind == 0) {
+    r = rho0 + ic.drho;
+  } else if (ic.kind == 1) {
+    const double dx = min_image(X[0] - ic.center[0], pl.dom[0]);
+    const double dy = min_image(X[1] - ic.center[1], pl.dom[1]);
+    const double R = ic.radius;
+    const double gg = exp(-(dx * dx + dy * dy) / (2.0 * R * R));
+    r = rho0 * (1.0 - ic.eps * ic.eps / (2.0 * cs2) * gg * gg);
+    ux += -ic.eps * (dy / R) * gg;
+    uy += ic.eps * (dx / R) * gg;
+  } else {
+    double r2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      const double d = min_image(X[a] - ic.center[a], pl.dom[a]);
+      r2 += d * d;
+    }
+    r = rho0 * (1.0 + ic.amplitude * exp(-r2 / (2.0 * ic.radius * ic.radius)));
+  }
+  rho[t] = r;
+  u[t] = ux;
+  u[N + t] = uy;
+  u[2 * N + t] = uz;
+}
 
 }  // namespace
 
@@ -226,6 +267,8 @@ int build_layout(lbm_ctx* h) {
     }
     if (!any) return LBM_EINVAL;
     v.tau = 2.0 * p.tau - 0.5;  // eq. rescTau
+    v.h = p.h / 2.0;
+    for (int a = 0; a < 3; ++a) v.origin[a] = v.boxed[a] ? p.origin[a] + v.lo[a] * p.h : p.origin[a];
   }
   return LBM_OK;
 }
@@ -647,6 +690,111 @@ int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* 
     h->ready = true;
   }
   return LBM_OK;
+}
+
+int lbm_init_analytic(lbm_handle h, int run, const lbm_ic* ic) {
+  if (!h || !ic || run < 0 || run >= h->batch || ic->kind < 0 || ic->kind > 2) return LBM_EINVAL;
+  if (ic->kind != LBM_IC_UNIFORM && !(ic->radius > 0.0)) return LBM_EINVAL;
+  if (h->ready) {
+    std::fill(h->inited.begin(), h->inited.end(), 0);
+    h->ready = false;
+  }
+  ICDesc d{};
+  d.kind = ic->kind;
+  for (int a = 0; a < 3; ++a) {
+    d.u0[a] = ic->u0[a];
+    d.center[a] = ic->center[a];
+  }
+  d.radius = ic->radius;
+  d.amplitude = ic->amplitude;
+  d.eps = ic->eps;
+  d.drho = ic->drho;
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& v = h->lev[l];
+    const long long N = v.n_nodes;
+    double* buf = (double*)h->dalloc(sizeof(double) * 4 * N);
+    if (!buf) return LBM_ENOMEM;
+    Placement pl{};
+    for (int a = 0; a < 3; ++a) {
+      pl.origin[a] = v.origin[a];
+      pl.dom[a] = h->lev[0].n[a];
+    }
+    pl.h = v.h;
+    k_ic_fields<<<(unsigned)((N + 127) / 128), 128, 0, h->stream>>>(v.view, pl, d, h->cfg.rho0,
+                                                                    h->D, buf, buf + N);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = h->ops.init(v.view, h->cfg.storage, run, buf, buf + N, h->ref, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->launches += 2;
+    h->dfree(buf);
+    if (e != cudaSuccess) {
+      snprintf(g_errmsg, sizeof(g_errmsg), "init_analytic: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+    h->inited[(size_t)l * h->batch + run] = 1;
+  }
+  if (std::all_of(h->inited.begin(), h->inited.end(), [](char c) { return c != 0; })) {
+    for (int l = 0; l < h->nlev; ++l) {
+      h->lev[l].last = 0;
+      h->lev[l].nsteps = 0;
+    }
+    h->coarse_steps = 0;
+    h->seeded = false;
+    h->ready = true;
+  }
+  return LBM_OK;
+}
+
+int lbm_noise(lbm_handle refined, lbm_handle single, int run, int margin, double* max_abs,
+              double* rms, long long* count) {
+  if (!refined || !single || !max_abs || !rms || run < 0 || run >= refined->batch ||
+      run >= single->batch || margin < 0)
+    return LBM_EINVAL;
+  if (refined->nlev < 2 || refined->cfg.lattice != single->cfg.lattice ||
+      refined->cfg.storage != single->cfg.storage)
+    return LBM_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (refined->lev[0].n[a] != single->lev[0].n[a]) return LBM_EINVAL;
+  if (!refined->ready || !single->ready) return LBM_ESTATE;
+  CK(cudaStreamSynchronize(single->stream));
+  const Level& va = refined->lev[0];
+  const Level& vb = single->lev[0];
+  const Level& c = refined->lev[1];
+  NoiseRegion reg{};
+  for (int a = 0; a < 3; ++a) {
+    reg.boxed[a] = c.boxed[a];
+    reg.lo[a] = c.lo[a];
+    reg.E[a] = c.hi[a] - c.lo[a];
+    reg.n[a] = va.n[a];
+  }
+  reg.margin = margin;
+  const int nb = (int)((va.n_nodes + kDiagThreads - 1) / kDiagThreads);
+  double* part = (double*)refined->dalloc(sizeof(double) * 3 * nb);
+  if (!part) return LBM_ENOMEM;
+  std::vector<double> hp((size_t)3 * nb);
+  cudaError_t e = refined->ops.noise_partial(va.view, va.last, refined->ref, vb.view, vb.last,
+                                             single->ref, refined->cfg.storage, run, reg, part,
+                                             nb, refined->stream);
+  ++refined->launches;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
+                        refined->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(refined->stream);
+  refined->dfree(part);
+  if (e != cudaSuccess) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "noise: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  double mx = 0.0, ss = 0.0, cnt = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    mx = std::max(mx, hp[b]);
+    ss += hp[(size_t)nb + b];
+    cnt += hp[(size_t)2 * nb + b];
+  }
+  *max_abs = mx;
+  *rms = cnt > 0 ? std::sqrt(ss / cnt) : 0.0;
+  if (count) *count = (long long)cnt;
+  return std::isfinite(mx) ? LBM_OK : LBM_EUNSTABLE;
 }
 
 int lbm_set_graphs(lbm_handle h, int enable) {

@@ -34,6 +34,10 @@ struct Ops {
                              const RefState& ref, cudaStream_t s);
   cudaError_t (*diag_partial)(const LevelView& v, int storage, int run, int last, double* partial,
                               int nblocks, const RefState& ref, cudaStream_t s);
+  cudaError_t (*noise_partial)(const LevelView& a, int last_a, const RefState& ra,
+                               const LevelView& b, int last_b, const RefState& rb, int storage,
+                               int run, const NoiseRegion& reg, double* partial, int nblocks,
+                               cudaStream_t s);
   cudaError_t (*probe)(const LevelView& v, int storage, int last, const int* ijk, int n,
                        double* rec, int cap, unsigned long long* counter, const RefState& ref,
                        cudaStream_t s);

@@ -33,8 +33,9 @@ RefF make_ref_f(const RefState& r) {
 
 template <class L, class S, int COLL>
 cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, cudaStream_t s) {
+  constexpr int NPT = K1Tune<L, S>::NPT;
   dim3 block(32, 4, 1);
-  dim3 grid((v.n[0] + 31) / 32, (v.n[1] + 3) / 4, v.n[2] * v.batch);
+  dim3 grid((v.n[0] + 31) / 32, (v.n[1] + 4 * NPT - 1) / (4 * NPT), v.n[2] * v.batch);
   const bool mov = ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
@@ -186,6 +187,19 @@ cudaError_t diag_partial(const LevelView& v, int storage, int run, int last, dou
 }
 
 template <class L>
+cudaError_t noise_partial(const LevelView& a, int last_a, const RefState& ra, const LevelView& b,
+                          int last_b, const RefState& rb, int storage, int run,
+                          const NoiseRegion& reg, double* partial, int nblocks, cudaStream_t s) {
+  if (storage == 0)
+    k_noise_partial<L, float><<<nblocks, kDiagThreads, 0, s>>>(a, last_a, ra, b, last_b, rb, run,
+                                                               reg, partial);
+  else
+    k_noise_partial<L, __half><<<nblocks, kDiagThreads, 0, s>>>(a, last_a, ra, b, last_b, rb,
+                                                                run, reg, partial);
+  return cudaGetLastError();
+}
+
+template <class L>
 cudaError_t probe(const LevelView& v, int storage, int last, const int* ijk, int n, double* rec,
                   int cap, unsigned long long* counter, const RefState& ref, cudaStream_t s) {
   if (storage == 0)
@@ -211,6 +225,7 @@ Ops make_ops() {
   o.macros_f = detail::macros_f<L>;
   o.populations = detail::populations<L>;
   o.diag_partial = detail::diag_partial<L>;
+  o.noise_partial = detail::noise_partial<L>;
   o.probe = detail::probe<L>;
   return o;
 }

@@ -44,6 +44,16 @@ class lbm_config(ctypes.Structure):
                 ("u_ref", ctypes.c_double * 3)]
 
 
+class lbm_ic(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double * 3),
+                ("center", ctypes.c_double * 3), ("radius", ctypes.c_double),
+                ("amplitude", ctypes.c_double), ("eps", ctypes.c_double),
+                ("drho", ctypes.c_double)]
+
+
+IC_KINDS = {"uniform": 0, "vortex": 1, "pulse": 2}
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -81,6 +91,9 @@ def lib():
     L.lbm_probe.argtypes = [P, dp, ctypes.c_int, ip]
     L.lbm_diag.argtypes = [P, ctypes.c_int, dp, dp]
     L.lbm_diag_noalloc.argtypes = [P, ctypes.c_int, dp, dp]
+    L.lbm_init_analytic.argtypes = [P, ctypes.c_int, ctypes.POINTER(lbm_ic)]
+    L.lbm_noise.argtypes = [P, P, ctypes.c_int, ctypes.c_int, dp, dp,
+                            ctypes.POINTER(ctypes.c_longlong)]
     L.lbm_sync.argtypes = [P]
     L.lbm_kernel_launches.argtypes = [P]
     L.lbm_kernel_launches.restype = ctypes.c_longlong
@@ -215,6 +228,32 @@ class Lbm:
         if rho.size != self.nodes(level) or u.shape[1] != rho.size:
             raise ValueError("field size does not match the level")
         _check(lib().lbm_init(self._h, level, run, _dp(rho), _dp(u)), "lbm_init")
+
+    def init_analytic(self, ic: dict, run=0):
+        """Device-side initial state from a workload IC description
+        (kind uniform / vortex / pulse, as in workloads.initial_fields)."""
+        d = lbm_ic()
+        d.kind = IC_KINDS[ic["kind"]]
+        for a, v in enumerate(ic.get("u0", (0.0, 0.0, 0.0))):
+            d.u0[a] = float(v)
+        for a, v in enumerate(ic.get("center", (0.0, 0.0, 0.0))):
+            d.center[a] = float(v)
+        d.radius = float(ic.get("radius", 0.0))
+        d.amplitude = float(ic.get("amplitude", 0.0))
+        d.eps = float(ic.get("eps", 0.0))
+        d.drho = float(ic.get("drho", 0.0))
+        _check(lib().lbm_init_analytic(self._h, run, ctypes.byref(d)), "lbm_init_analytic")
+
+    def noise(self, single: "Lbm", run=0, margin=4):
+        """(max, rms, nodes) of |rho - rho_single| outside the refined box."""
+        mx = ctypes.c_double()
+        rms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        rc = lib().lbm_noise(self._h, single._h, run, margin, ctypes.byref(mx),
+                             ctypes.byref(rms), ctypes.byref(n))
+        if rc not in (LBM_OK, -4):
+            _check(rc, "lbm_noise")
+        return mx.value, rms.value, n.value
 
     def step(self, n=1):
         _check(lib().lbm_step(self._h, int(n)), "lbm_step")
