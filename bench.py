@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="runs per GPU (0: enough to exceed L2 4x)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", type=int, default=48, help="requests of the serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -367,6 +369,28 @@ def main():
                            "dominant_kernel_frac": round(vb / (vt / vn * 1e-3) / 1e9 / peak, 4)}
         gv.close()
 
+    # ---------------- serving: continuous batching vs one run at a time -----
+    serving = None
+    if args.serve > 0:
+        from paper_2004_11863_gb300 import serve as SV
+        reqs = W.serving_requests(args.serve, rate=args.serve_rate, step_scale=0.1,
+                                  size_scale=0.5)
+        served = SV.Server(hbm_budget=32e9, max_active=32, streams=16, chunk=25,
+                           storage="fp16").run(reqs)
+        seq = SV.serve_sequential(reqs, storage="fp32")
+        serving = {
+            "requests": args.serve, "arrival_rate_per_s": args.serve_rate,
+            "stream": "seeded mix of D2Q9/D3Q19/D3Q27, 1-3 levels, Ma 0.05-0.2, "
+                      "tau-1/2 in [1e-5,1e-2], vortex/pulse; sides x0.5, steps x0.1",
+            "served_fp16": {"runs_per_s": round(served["runs_per_s"], 2),
+                            "p50_s": round(served["p50_s"], 4), "p99_s": round(served["p99_s"], 4),
+                            "unstable": served["unstable"],
+                            "max_concurrent": served["max_concurrent"]},
+            "sequential_fp32": {"runs_per_s": round(seq["runs_per_s"], 2),
+                                "p50_s": round(seq["p50_s"], 4), "p99_s": round(seq["p99_s"], 4),
+                                "unstable": seq["unstable"]},
+        }
+
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline(case)
@@ -396,6 +420,7 @@ def main():
         "gpu_launches": int(launches),
         "e2e": e2e,
         "variants": variants,
+        "serving": serving,
         "cpu_baseline": cpu,
         "stable": bool(stable),
     }

@@ -127,6 +127,12 @@ typedef struct {
 int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
                lbm_handle* out);
 
+/* Device bytes lbm_create would allocate for this configuration (level
+ * populations and interface histories), computed on the host without
+ * touching the device; for admission against a memory budget.  Returns
+ * LBM_EINVAL for a layout lbm_create would reject. */
+int lbm_bytes(const lbm_config* cfg, unsigned long long* bytes);
+
 /* Level geometry: node counts n[3], relaxation time tau_l, and the number of
  * active nodes (nodes that are updated; the parent nodes strictly inside a
  * child's restriction ring are inactive).  Any output pointer may be NULL. */

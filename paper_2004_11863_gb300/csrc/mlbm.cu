@@ -640,6 +640,35 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
   return LBM_OK;
 }
 
+int lbm_bytes(const lbm_config* cfg, unsigned long long* bytes) {
+  if (!cfg || !bytes) return LBM_EINVAL;
+  if (cfg->lattice < 0 || cfg->lattice > 2 || cfg->nlevels < 1 ||
+      cfg->nlevels > LBM_MAX_LEVELS || cfg->batch < 1 || cfg->storage < 0 || cfg->storage > 1)
+    return LBM_EINVAL;
+  lbm_ctx* h = new (std::nothrow) lbm_ctx();
+  if (!h) return LBM_ENOMEM;
+  h->cfg = *cfg;
+  h->ops = ops_for(cfg->lattice);
+  h->q = h->ops.q;
+  h->D = h->ops.d;
+  h->nlev = cfg->nlevels;
+  h->batch = cfg->batch;
+  int rc = build_layout(h);
+  unsigned long long total = 0;
+  if (rc == LBM_OK) {
+    for (int l = 0; l < h->nlev; ++l) build_view(h, l);
+    for (int l = 1; l < h->nlev; ++l) build_interface(h, l);
+    for (int l = 0; l < h->nlev; ++l) {
+      total += h->lev[l].bytes;
+      if (l >= 1)
+        total += sizeof(float) * 3ull * h->lev[l].ring.nv * h->lev[l].ring.K * h->batch;
+    }
+    *bytes = total;
+  }
+  delete h;
+  return rc;
+}
+
 int lbm_level_info(lbm_handle h, int level, int* n, double* tau, long long* n_active) {
   if (!h || level < 0 || level >= h->nlev) return LBM_EINVAL;
   const Level& v = h->lev[level];

@@ -91,6 +91,7 @@ def lib():
     L.lbm_probe.argtypes = [P, dp, ctypes.c_int, ip]
     L.lbm_diag.argtypes = [P, ctypes.c_int, dp, dp]
     L.lbm_diag_noalloc.argtypes = [P, ctypes.c_int, dp, dp]
+    L.lbm_bytes.argtypes = [ctypes.POINTER(lbm_config), ctypes.POINTER(ctypes.c_ulonglong)]
     L.lbm_init_analytic.argtypes = [P, ctypes.c_int, ctypes.POINTER(lbm_ic)]
     L.lbm_noise.argtypes = [P, P, ctypes.c_int, ctypes.c_int, dp, dp,
                             ctypes.POINTER(ctypes.c_longlong)]
@@ -149,6 +150,15 @@ def make_config(lattice: str, collision: str, tau0: float, dims: Sequence[int], 
     for a in range(3):
         c.u_ref[a] = float(u_ref[a])
     return c
+
+
+def lbm_bytes(lattice, collision, tau0, dims, boxes, storage="fp32", batch=1, rho0=1.0,
+              u_ref=(0.0, 0.0, 0.0)) -> int:
+    """Device bytes a run of this layout needs (no device work)."""
+    cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0, u_ref)
+    b = ctypes.c_ulonglong()
+    _check(lib().lbm_bytes(ctypes.byref(cfg), ctypes.byref(b)), "lbm_bytes")
+    return int(b.value)
 
 
 class _TorchAllocator:

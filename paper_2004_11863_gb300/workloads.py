@@ -259,3 +259,71 @@ CONFIGS = {
 def updates_per_coarse_step(case: Case, active_counts: Sequence[int]) -> int:
     """Node updates per coarse step, each level at its own rate: sum 2^l N_l."""
     return int(sum((2 ** l) * int(n) for l, n in enumerate(active_counts)))
+
+
+# --------------------------------------------------------------------------
+# Serving stream: mixed runs arriving as a Poisson process.
+# --------------------------------------------------------------------------
+
+def _central_half_boxes(dim: int, side: int, nlevels: int):
+    """Each child box covers the central half of its parent on every axis."""
+    boxes = []
+    n = side  # parent node count per axis (level 0: periodic, side nodes)
+    for l in range(1, nlevels):
+        if l == 1:
+            lo, hi = n // 4, n - n // 4
+            nc = 2 * (hi - lo) + 1
+        else:
+            lo, hi = n // 4, n - 1 - n // 4
+            nc = 2 * (hi - lo) + 1
+        boxes.append((tuple([lo] * dim + [0] * (3 - dim)),
+                      tuple([hi] * dim + [1] * (3 - dim))))
+        n = nc
+    return boxes
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float     # seconds after the stream starts
+    case: Case
+
+
+def serving_requests(n: int, rate: float, seed: int = 20041186, step_scale: float = 1.0,
+                     size_scale: float = 1.0) -> List[Request]:
+    """Seeded request stream shaped like the serving workload: lattice D2Q9
+    (1/2), D3Q19 (1/4), D3Q27 (1/4); 2D coarse side in {64, 80, .., 1024},
+    3D in {48, 64, .., 160}; 1-3 levels, each child box the central half of
+    its parent; Mach 0.05-0.2 along x; tau_c - 1/2 log-uniform in
+    [1e-5, 1e-2]; vortex or pulse (1/2 each); 100-1000 coarse steps; RR.
+    Arrivals are a Poisson process of `rate` requests per second.
+    step_scale / size_scale shrink steps and sides for bounded test runs."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += rng.exponential(1.0 / rate)
+        lat = rng.choice(["D2Q9", "D3Q19", "D3Q27"], p=[0.5, 0.25, 0.25])
+        dim = DIM_OF[lat]
+        if dim == 2:
+            side = int(rng.choice(np.arange(64, 1025, 16)))
+        else:
+            side = int(rng.choice(np.arange(48, 161, 16)))
+        side = max(48 if dim == 3 else 64, int(round(side * size_scale / 16)) * 16)
+        nlev = int(rng.integers(1, 4))
+        ma = rng.uniform(0.05, 0.2)
+        tau0 = 0.5 + 10.0 ** rng.uniform(-5, -2)
+        steps = max(4, int(round(rng.integers(100, 1001) * step_scale)))
+        u0 = (ma * CS, 0.0, 0.0)
+        c = side / 2.0
+        if rng.random() < 0.5:
+            ic = dict(kind="vortex", u0=u0, center=(c * 0.6, c, 0.0), radius=side / 24.0,
+                      eps=0.05 * CS)
+        else:
+            ic = dict(kind="pulse", u0=u0, center=(c * 0.6, c, c if dim == 3 else 0.0),
+                      radius=side / 32.0, amplitude=1e-3)
+        dims = (side, side, side if dim == 3 else 1)
+        case = Case(f"req{k}", lat, "RR", float(tau0), dims,
+                    _central_half_boxes(dim, side, nlev), ic, steps)
+        out.append(Request(k, t, case))
+    return out
