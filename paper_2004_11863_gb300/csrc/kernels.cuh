@@ -391,7 +391,7 @@ __global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new,
 // tile instead of once per stencil use.
 template <class L>
 struct InjTile {
-  static constexpr int TI = (L::D == 3) ? 32 : 128;  // along the first tangent axis
+  static constexpr int TI = (L::D == 3) ? 32 : 64;  // along the first tangent axis
   static constexpr int TJ = (L::D == 3) ? 8 : 1;     // along the second
   static constexpr int WI = TI / 2 + 5;              // parent window (stencil reach)
   static constexpr int WJ = (L::D == 3) ? TJ / 2 + 5 : 1;

@@ -122,7 +122,8 @@ struct lbm_ctx {
   // side stream per level: a parent's update runs there, beside its child's
   // second sub-step (they touch disjoint memory)
   cudaStream_t side[LBM_MAX_LEVELS] = {};
-  cudaEvent_t ev_fork[LBM_MAX_LEVELS] = {}, ev_join[LBM_MAX_LEVELS] = {};
+  cudaEvent_t ev_fork[LBM_MAX_LEVELS] = {}, ev_join[LBM_MAX_LEVELS] = {},
+              ev_restrict[LBM_MAX_LEVELS] = {};
   bool has_alloc = false;
   lbm_allocator alloc{};
   Level lev[LBM_MAX_LEVELS];
@@ -214,6 +215,7 @@ void release(lbm_ctx* h) {
     if (h->side[l]) cudaStreamDestroy(h->side[l]);
     if (h->ev_fork[l]) cudaEventDestroy(h->ev_fork[l]);
     if (h->ev_join[l]) cudaEventDestroy(h->ev_join[l]);
+    if (h->ev_restrict[l]) cudaEventDestroy(h->ev_restrict[l]);
   }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   h->event_pool.clear();
@@ -430,7 +432,7 @@ inline float omega_of(double tau) { return (float)(1.0 - 1.0 / tau); }
 #define LAUNCH(expr) LAUNCH_K(-1, -1, expr)
 
 // One step of level l with its finer levels (see the file comment).
-int advance(lbm_ctx* h, int l, const float* wt, bool launch) {
+int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_before_update) {
   Level& v = h->lev[l];
   const int st = h->cfg.storage;
   const RefState& ref = h->ref;
@@ -445,12 +447,13 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch) {
     Level& c = h->lev[l + 1];
     c.head = (c.head + 1) % 3;
     LAUNCH_K(1, l, h->ops.capture(v.view, c.ring, st, par, 0, c.head, c.head, ref, h->cur));
-    int rc = advance(h, l + 1, v.nsteps == 0 ? kTimeLin : kTimeQuad, launch);
+    int rc = advance(h, l + 1, v.nsteps == 0 ? kTimeLin : kTimeQuad, launch, nullptr);
     if (rc) return rc;
-    const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
-    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref, h->cur));
-    // Level l's own update needs nothing the child's second sub-step
-    // produces and touches none of its memory: run it on the side stream
+    // The restriction and level l's own update need nothing the child's
+    // second sub-step produces and touch none of the memory it writes,
+    // except that the child's second update overwrites the cells the
+    // restriction reads: run restriction + level-l update on the side
+    // stream, and let the child's update wait for the restriction only
     // (serialised while profiling, so each kernel is timed alone).
     cudaStream_t main = h->cur;
     const bool fork = launch && !h->profiling;
@@ -459,6 +462,12 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch) {
       CK(cudaStreamWaitEvent(h->side[l], h->ev_fork[l], 0));
       h->cur = h->side[l];
     }
+    const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
+    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref, h->cur));
+    if (fork) CK(cudaEventRecord(h->ev_restrict[l], h->side[l]));
+    // (this level may itself be a second sub-step whose update must wait
+    // for its parent's restriction)
+    if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
     LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
                                          h->cur));
     if (fork) {
@@ -467,11 +476,12 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch) {
     }
     v.last = par;
     v.nsteps++;
-    rc = advance(h, l + 1, kTimeDirect, launch);
+    rc = advance(h, l + 1, kTimeDirect, launch, fork ? h->ev_restrict[l] : nullptr);
     if (rc) return rc;
     if (fork) CK(cudaStreamWaitEvent(main, h->ev_join[l], 0));
     return LBM_OK;
   }
+  if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
   LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref, h->cur));
   v.last = par;
   v.nsteps++;
@@ -487,7 +497,7 @@ int probe_launch(lbm_ctx* h, bool launch) {
 }
 
 int coarse_step(lbm_ctx* h, bool launch) {
-  int rc = advance(h, 0, nullptr, launch);
+  int rc = advance(h, 0, nullptr, launch, nullptr);
   if (rc) return rc;
   return probe_launch(h, launch);
 }
@@ -624,7 +634,8 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
   for (int l = 0; l < h->nlev && ok; ++l)
     ok = cudaStreamCreateWithFlags(&h->side[l], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->ev_fork[l], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_restrict[l], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     release(h);
     delete h;

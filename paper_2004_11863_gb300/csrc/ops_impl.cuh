@@ -73,11 +73,11 @@ template <class L>
 cudaError_t capture(const LevelView& p, const RingDesc& R, int storage, int par, int mode,
                     int s_new, int s_also, const RefState& ref, cudaStream_t s) {
   if (R.K == 0) return cudaSuccess;
-  dim3 grid(blocks_for(R.K, 128), p.batch);
+  dim3 grid(blocks_for(R.K, 64), p.batch);
   if (storage == 0)
-    k_capture<L, float><<<grid, 128, 0, s>>>(p, R, par, mode, s_new, s_also, make_ref_f<L>(ref));
+    k_capture<L, float><<<grid, 64, 0, s>>>(p, R, par, mode, s_new, s_also, make_ref_f<L>(ref));
   else
-    k_capture<L, __half><<<grid, 128, 0, s>>>(p, R, par, mode, s_new, s_also, make_ref_f<L>(ref));
+    k_capture<L, __half><<<grid, 64, 0, s>>>(p, R, par, mode, s_new, s_also, make_ref_f<L>(ref));
   return cudaGetLastError();
 }
 

@@ -242,3 +242,22 @@ def test_probe_records_every_coarse_step(M):
         idx = j * n[0] + i
         assert abs(rec[-1, 0, k, 0] - rho[idx]) < TOL32
         assert abs(rec[-1, 0, k, 1] - u[0, idx]) < TOL32
+
+
+def test_reflected_acoustic_wave_matches_oracle(M):
+    """The GPU reproduces the oracle's reflected-wave ratio of the convected
+    1D acoustic wave (Sec. 9.2) and its fields within 1e-6."""
+    from tests.test_oracle_pins import e5_case, e5_fields, e5_ratio
+    case = e5_case("RR")
+    g = M.Lbm(case.lattice, case.collision, case.tau0, case.dims, case.boxes, u_ref=case.u_ref)
+    o = oracle.Run(case.lattice, case.collision, case.tau0, case.dims, case.boxes)
+    for l in range(2):
+        g.init(l, 0, *e5_fields(case, l))
+        o.init_level(l, *e5_fields(case, l))
+    o.init_done()
+    g.step(case.steps)
+    o.step(case.steps)
+    compare(g, o, 2)
+    gi, _, gr, _ = e5_ratio(g.macros(0)[0], g.macros(1)[0], case)
+    oi, _, orf, _ = e5_ratio(o.macros(0)[0], o.macros(1)[0], case)
+    assert abs(gr / gi - orf / oi) < 0.02 * (orf / oi)

@@ -429,3 +429,57 @@ def test_smooth_wave_crosses_interface_like_uniform_grid(coll):
     m = ~np.isnan(res[1])
     err = np.max(np.abs(res[1][m] - res[0][m]))
     assert err < 2e-6, err  # 2% of the 1e-4 amplitude
+
+
+# ------------------------------------------------------ printed outcome check
+
+def e5_case(collision):
+    """Convected 1D acoustic wave of Sec. 9.2 (eq. init_Pulse): A = 1e-4,
+    R = 5, x_c = 750, U = 0.1 c_s, nu = 1e-6, fine level on x in [500, 1000]
+    (periodic domain of 1000 coarse cells, 4 cells across)."""
+    return W.Case("e5", "D2Q9", collision, 0.5 + 3e-6, (1000, 4, 1),
+                  [((500, 0, 0), (1000, 4, 1))], dict(kind="uniform", u0=(0.1 * W.CS, 0, 0)), 900)
+
+
+def e5_fields(case, level):
+    X, _, _ = W.level_coords(case, level)
+    rp = 1e-4 * np.exp(-(X - 750.0) ** 2 / 50.0)
+    u = np.zeros((3, X.size))
+    u[0] = 0.1 * W.CS - rp * W.CS  # left-going: u' = -rho' c_s / rho0
+    return 1.0 + rp, u
+
+
+def e5_ratio(rho0, rho1, case):
+    X0, _, _ = W.level_coords(case, 0)
+    X1, _, _ = W.level_coords(case, 1)
+    m0 = ~np.isnan(rho0)
+    inc = np.max(rho0[m0] - 1.0)
+    xi = X0[m0][np.argmax(rho0[m0] - 1.0)]
+    sel = (X1 > 520) & (X1 < 990)
+    refl = np.max(np.abs(rho1[sel] - 1.0))
+    xr = X1[sel][np.argmax(np.abs(rho1[sel] - 1.0))]
+    return inc, xi, refl, xr
+
+
+def test_reflected_acoustic_wave_order_of_magnitude():
+    """The paper reports the acoustic wave reflected where a convected 1D
+    pulse leaves the fine level at about 1/2000 of the incident amplitude,
+    the same for BGK and RR (Sec. 9.2).  The oracle must land within a
+    factor 3 of that, with the incident peak near x = 270 at t = 900 and the
+    reflected peak where a right-going wave from the interface would be."""
+    out = {}
+    for coll in ("BGK", "RR"):
+        case = e5_case(coll)
+        r = oracle.Run(case.lattice, case.collision, case.tau0, case.dims, case.boxes)
+        for l in range(2):
+            r.init_level(l, *e5_fields(case, l))
+        r.init_done()
+        r.step(case.steps)
+        out[coll] = e5_ratio(r.macros(0)[0], r.macros(1)[0], case)
+    inc, xi, refl, xr = out["RR"]
+    assert abs(xi - (750 - 900 * 0.9 * W.CS)) < 3.0
+    t_hit = 250.0 / (0.9 * W.CS)
+    assert abs(xr - (500 + (900 - t_hit) * 1.1 * W.CS)) < 5.0
+    ratio = refl / inc
+    assert 1.0 / 6000 < ratio < 3.0 / 2000, 1 / ratio
+    assert abs(out["BGK"][2] - out["RR"][2]) < 1e-3 * out["RR"][2]
