@@ -23,7 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 LATTICE = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISION = {"BGK": 0, "REG": 1, "RR": 2}
+COLLISION = {"BGK": 0, "REG": 1, "RR": 2, "HRR": 3}
 
 
 def build(force: bool = False) -> str:
@@ -50,6 +50,8 @@ def lib():
             L.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
             L.orc_a1.argtypes = [ctypes.c_int, dp, dp]
             L.orc_collide.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+            L.orc_collide_hrr.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          dp, dp, dp]
             L.orc_interp_time.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
             L.orc_interp_time.restype = ctypes.c_double
             L.orc_interp_space.argtypes = [ctypes.c_double] * 4
@@ -70,6 +72,7 @@ def lib():
             L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_macros.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
             L.orc_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+            L.orc_set_sigma.argtypes = [ctypes.c_void_p, ctypes.c_double]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
@@ -119,6 +122,15 @@ def collide(name: str, collision: str, tau: float, f) -> np.ndarray:
     return out
 
 
+def collide_hrr(name: str, tau: float, sigma: float, f, S6) -> np.ndarray:
+    """H-RR collision with a given strain rate S6 = (xx, yy, zz, xy, xz, yz)."""
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+    S6 = np.ascontiguousarray(np.asarray(S6, dtype=np.float64).reshape(6))
+    out = np.zeros_like(f)
+    lib().orc_collide_hrr(LATTICE[name], float(tau), float(sigma), _dp(f), _dp(S6), _dp(out))
+    return out
+
+
 def interp_time(gm1, g0, gp1, first=False) -> float:
     return lib().orc_interp_time(gm1, g0, gp1, int(bool(first)))
 
@@ -151,8 +163,10 @@ class Run:
         self.nlevels = nlev
 
     @classmethod
-    def from_case(cls, case, init=True):
+    def from_case(cls, case, init=True, sigma=None):
         r = cls(case.lattice, case.collision, case.tau0, case.dims, case.boxes, case.rho0)
+        if sigma is not None:
+            r.set_sigma(sigma)
         if init:
             from paper_2004_11863_gb300 import workloads
             for l in range(r.nlevels):
@@ -192,6 +206,11 @@ class Run:
         _, N = self.dims(level)
         assert rho.size == N and u.shape[1] == N
         lib().orc_init_level(self._h, level, _dp(rho), _dp(u))
+
+    def set_sigma(self, sigma):
+        """Hybrid weight of the H-RR collision (call before init_done)."""
+        if lib().orc_set_sigma(self._h, float(sigma)) != 0:
+            raise ValueError("sigma must lie in [0, 1]")
 
     def init_done(self):
         lib().orc_init_done(self._h)

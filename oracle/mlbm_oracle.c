@@ -5,18 +5,17 @@
  * path.  It shares no code with the CUDA library.
  *
  * The scheme is written in population space with separate pre- and
- * post-collision arrays and follows the step list of Sec. 4.3 (cell-vertex
- * algorithm of Lagrava et al. with the overlap of Fig. Overlap), minus the
- * parts that only the hybrid model needs (steps 2e, 2f and the strain-rate
- * transfers).  Per step of level l:
- *   (2a/3a) stream the middle nodes of level l;
- *   (2b,2c,2g,2h / 3b,3c) rebuild the c->f boundary nodes (TF by temporal
- *       interpolation, IE by spatial interpolation) with eq. rescff;
+ * post-collision arrays and follows the cell-vertex algorithm of Sec. 4.3
+ * (Lagrava et al., with the overlap of Fig. Overlap); the hybrid model adds
+ * the velocity-gradient transfers of Sec. 4.4.  Per step of level l:
+ *   stream the middle nodes of level l;
+ *   rebuild the c->f boundary nodes (TF by temporal interpolation, IE by
+ *       spatial interpolation) with eq. rescff;
  *   if level l has a finer level: record the pre-collision state of level l
  *       on the finer box surface (coarse history at t+1), run the two finer
  *       sub-steps, then rebuild the f->c nodes (TN) with eqs. filterFneq and
- *       rescfc (step 3d);
- *   (2d,2i / 3e) collide every active node of level l.
+ *       rescfc (the restriction of the synchronous iteration);
+ *   collide every active node of level l.
  *
  * Readings taken where the paper is silent or garbled:
  *   - eq. TempInt prints its first point as t-1/2; the weights (-1/8,3/4,3/8)
@@ -253,6 +252,41 @@ static void collide_lat(const lattice_t* L, int coll, double tau,
   }
 }
 
+/* Hybrid recursive regularized collision (Sec. 3.3, eq. a1ij_HRR): the
+ * projected a1^(2) is blended with the finite-difference estimate of
+ * eq. stressT, a1 = sigma a1^(2) + (1 - sigma)(-2 tau rho cs^2 S); the
+ * third order follows by the recursion of eq. a13RR and the post-collision
+ * state by eq. f1RR in eq. LBMscheme_reg.  S6 = (xx, yy, zz, xy, xz, yz). */
+static void collide_hrr_lat(const lattice_t* L, double tau, double sigma, const double* f,
+                            const double* S6, double* out) {
+  double rho, u[3], feq[MAXQ];
+  moments(L, f, &rho, u);
+  feq_lat(L, rho, u, feq);
+  double a1p[3][3], a1[3][3], a3[3][3][3], zero1[3] = {0, 0, 0};
+  a1_lat(L, f, feq, a1p);
+  const double S[3][3] = {{S6[0], S6[3], S6[4]}, {S6[3], S6[1], S6[5]}, {S6[4], S6[5], S6[2]}};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      a1[a][b] = sigma * a1p[a][b] + (1.0 - sigma) * (-2.0 * tau * rho * CS2 * S[a][b]);
+  if (L->d == 2)
+    for (int a = 0; a < 3; ++a) a1[a][2] = a1[2][a] = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) {
+        a3[a][b][c] = u[a] * a1[b][c] + u[b] * a1[a][c] + u[c] * a1[a][b];
+        if (L->d == 2 && (a == 2 || b == 2 || c == 2)) a3[a][b][c] = 0.0;
+      }
+  const double om = 1.0 - 1.0 / tau;
+  for (int i = 0; i < L->q; ++i) out[i] = feq[i] + om * hermite_sum(L, i, 0.0, zero1, a1, a3);
+}
+
+void orc_collide_hrr(int lattice, double tau, double sigma, const double* f_in, const double* S6,
+                     double* f_out) {
+  lattice_t L;
+  build_lattice(lattice, &L);
+  collide_hrr_lat(&L, tau, sigma, f_in, S6, f_out);
+}
+
 void orc_collide(int lattice, int collision, double tau, const double* f_in,
                  double* f_out) {
   lattice_t L;
@@ -322,14 +356,25 @@ typedef struct {
   long* hidx;
   double* hist;
   long K;
+  /* Hybrid model (collision 3) only: pre-collision velocity per node
+   * [N][3]; strain rate each node last collided with [N][6] (xx, yy, zz,
+   * xy, xz, yz); strain rate handed to a TN node by the finer level [N][6];
+   * parent strain-rate history on this level's box surface [3][K][6]. */
+  double* vel;
+  double* sused;
+  double* sgiven;
+  double* hists;
 } level_t;
 
 struct orc_run {
   lattice_t L;
   int lattice, coll, nlev, dim;
   double rho0;
+  double sigma; /* hybrid weight of eq. a1ij_HRR (collision 3) */
   level_t lev[MAXLEV];
 };
+
+static void strain_fd(const orc_run* r, const level_t* v, int x, int y, int z, double* S6);
 
 static long nid(const level_t* v, int x, int y, int z) {
   return ((long)z * v->n[1] + y) * v->n[0] + x;
@@ -362,6 +407,10 @@ int orc_set_threads(int n) {
 }
 
 static void free_level(level_t* v) {
+  free(v->vel);
+  free(v->sused);
+  free(v->sgiven);
+  free(v->hists);
   free(v->fpost);
   free(v->fpre);
   free(v->cls);
@@ -432,7 +481,7 @@ static int build_history(orc_run* r, int l) {
 orc_run* orc_create(int lattice, int collision, double tau0, double rho0,
                     const int* dims, int nlevels, const int* boxes) {
   if (nlevels < 1 || nlevels > MAXLEV) return NULL;
-  if (collision < 0 || collision > 2) return NULL;
+  if (collision < 0 || collision > 3) return NULL;
   if (!(tau0 > 0.5)) return NULL;
   orc_run* r = (orc_run*)calloc(1, sizeof(orc_run));
   if (!r) return NULL;
@@ -445,6 +494,7 @@ orc_run* orc_create(int lattice, int collision, double tau0, double rho0,
   r->nlev = nlevels;
   r->dim = r->L.d;
   r->rho0 = rho0;
+  r->sigma = 1.0;
   for (int l = 0; l < nlevels; ++l) {
     level_t* v = &r->lev[l];
     if (l == 0) {
@@ -494,6 +544,12 @@ orc_run* orc_create(int lattice, int collision, double tau0, double rho0,
     v->fpre = (double*)calloc((size_t)v->N * r->L.q, sizeof(double));
     v->cls = (unsigned char*)malloc((size_t)v->N);
     if (!v->fpost || !v->fpre || !v->cls) goto fail;
+    if (collision == 3) {
+      v->vel = (double*)calloc((size_t)v->N * 3, sizeof(double));
+      v->sused = (double*)calloc((size_t)v->N * 6, sizeof(double));
+      v->sgiven = (double*)calloc((size_t)v->N * 6, sizeof(double));
+      if (!v->vel || !v->sused || !v->sgiven) goto fail;
+    }
     /* base classes: boundary layer of a refined level, middle otherwise */
     for (int z = 0; z < v->n[2]; ++z)
       for (int y = 0; y < v->n[1]; ++y)
@@ -511,6 +567,11 @@ orc_run* orc_create(int lattice, int collision, double tau0, double rho0,
     if (!any) goto fail; /* a child must be bounded on some axis */
     mark_child_footprint(r, l);
     if (build_history(r, l)) goto fail;
+    if (collision == 3) {
+      level_t* c = &r->lev[l + 1];
+      c->hists = (double*)calloc((size_t)3 * c->K * 6, sizeof(double));
+      if (!c->hists) goto fail;
+    }
   }
   return r;
 fail:
@@ -566,6 +627,31 @@ int orc_init_done(orc_run* r) {
       }
     }
   }
+  if (r->coll == 3) {
+    /* strain-rate history at t = 0 from the initial velocity field */
+    for (int l = 0; l < r->nlev; ++l) {
+      level_t* v = &r->lev[l];
+      for (long id = 0; id < v->N; ++id) {
+        double rho, u[3];
+        moments(&r->L, v->fpost + id * q, &rho, u);
+        for (int a = 0; a < 3; ++a) v->vel[id * 3 + a] = u[a];
+      }
+    }
+    for (int l = 0; l + 1 < r->nlev; ++l) {
+      level_t* p = &r->lev[l];
+      level_t* c = &r->lev[l + 1];
+      for (int z = 0; z < p->n[2]; ++z)
+        for (int y = 0; y < p->n[1]; ++y)
+          for (int x = 0; x < p->n[0]; ++x) {
+            long k = c->hidx[nid(p, x, y, z)];
+            if (k < 0) continue;
+            double S6[6];
+            strain_fd(r, p, x, y, z, S6);
+            for (int sl = 1; sl <= 2; ++sl)
+              memcpy(c->hists + ((size_t)sl * c->K + k) * 6, S6, sizeof(S6));
+          }
+    }
+  }
   return 0;
 }
 
@@ -612,7 +698,8 @@ static void hist_at(const orc_run* r, const level_t* p, const level_t* c,
   }
 }
 
-/* Steps 2b/2c/2g/2h (wt = temporal weights) or 3b/3c (wt = {0,0,1}):
+/* Asynchronous fine sub-step (wt = temporal weights) or synchronous one
+ * (wt = {0,0,1}):
  * rebuild every TF/IE node of level l from the parent history. */
 static void rebuild_boundary(orc_run* r, int l, const double* wt) {
   level_t* c = &r->lev[l];
@@ -662,7 +749,8 @@ static void rebuild_boundary(orc_run* r, int l, const double* wt) {
 }
 
 /* Record the parent's pre-collision (rho, u, f^(1)) at t+1 on the child
- * box surface, shifting the older slots down (step 2 of Sec. 4.3). */
+ * box surface, shifting the older slots down (Sec. 4.3, before the fine
+ * sub-steps). */
 static void capture_history(orc_run* r, int l) {
   level_t* p = &r->lev[l];
   level_t* c = &r->lev[l + 1];
@@ -688,7 +776,7 @@ static void capture_history(orc_run* r, int l) {
   }
 }
 
-/* Step 3d: filter the child's pre-collision f^(1) around the node
+/* Restriction: filter the child's pre-collision f^(1) around the node
  * co-located with each TN node (eq. filterFneq) and rebuild the TN node
  * with eq. rescfc from the co-located child node's rho and u. */
 static void restrict_tn(orc_run* r, int l) {
@@ -743,6 +831,195 @@ static void collide_level(orc_run* r, level_t* v) {
   }
 }
 
+/* ---------------- hybrid model (collision 3): Sec. 4.4 ------------------ */
+
+/* Pre-collision velocity of every active node of a level. */
+static void velocity_field(orc_run* r, level_t* v) {
+  const int q = r->L.q;
+#pragma omp parallel for schedule(static)
+  for (long id = 0; id < v->N; ++id) {
+    if (v->cls[id] == C_INACTIVE) continue;
+    double rho, u[3];
+    moments(&r->L, v->fpre + id * q, &rho, u);
+    for (int a = 0; a < 3; ++a) v->vel[id * 3 + a] = u[a];
+  }
+}
+
+/* Second-order central differences of the velocity field:
+ * S_ab = (d_a u_b + d_b u_a) / 2, d_a u ~ (u(x+e_a) - u(x-e_a)) / 2. */
+static void strain_fd(const orc_run* r, const level_t* v, int x, int y, int z, double* S6) {
+  double g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}; /* g[a][b] = d_a u_b */
+  const int X[3] = {x, y, z};
+  for (int a = 0; a < r->dim; ++a) {
+    int P[3] = {X[0], X[1], X[2]}, M[3] = {X[0], X[1], X[2]};
+    P[a] += 1;
+    M[a] -= 1;
+    if (v->per[a]) {
+      P[a] = wrap(P[a], v->n[a]);
+      M[a] = wrap(M[a], v->n[a]);
+    }
+    const double* up = v->vel + nid(v, P[0], P[1], P[2]) * 3;
+    const double* um = v->vel + nid(v, M[0], M[1], M[2]) * 3;
+    for (int b = 0; b < 3; ++b) g[a][b] = 0.5 * (up[b] - um[b]);
+  }
+  S6[0] = g[0][0];
+  S6[1] = g[1][1];
+  S6[2] = g[2][2];
+  S6[3] = 0.5 * (g[0][1] + g[1][0]);
+  S6[4] = 0.5 * (g[0][2] + g[2][0]);
+  S6[5] = 0.5 * (g[1][2] + g[2][1]);
+}
+
+/* Collide the middle and TN nodes of a level: S from finite differences,
+ * or, at TN nodes, the strain rate handed down by the finer level after the
+ * restriction (Sec. 4.4, synchronous iteration). */
+static void collide_interior_hrr(orc_run* r, level_t* v) {
+  const int q = r->L.q;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < v->n[2]; ++z)
+    for (int y = 0; y < v->n[1]; ++y)
+      for (int x = 0; x < v->n[0]; ++x) {
+        long id = nid(v, x, y, z);
+        if (v->cls[id] != C_MIDDLE && v->cls[id] != C_TN) continue;
+        double S6[6];
+        if (v->cls[id] == C_TN)
+          memcpy(S6, v->sgiven + id * 6, sizeof(S6));
+        else
+          strain_fd(r, v, x, y, z, S6);
+        memcpy(v->sused + id * 6, S6, sizeof(S6));
+        collide_hrr_lat(&r->L, v->tau, r->sigma, v->fpre + id * q, S6, v->fpost + id * q);
+      }
+}
+
+/* Sec. 4.4, asynchronous iteration, after the fine middle collision: the
+ * parent velocity at its TN nodes at t+1 from a fictitious streaming of the
+ * child's post-collision state over the co-located child node's
+ * neighbours, then the parent strain rate at t+1 on the child box surface
+ * by finite differences, stored as the newest strain-rate history slot. */
+static void parent_strain(orc_run* r, int l) {
+  level_t* p = &r->lev[l];
+  level_t* c = &r->lev[l + 1];
+  const lattice_t* L = &r->L;
+  const int q = L->q;
+  for (int z = 0; z < p->n[2]; ++z)
+    for (int y = 0; y < p->n[1]; ++y)
+      for (int x = 0; x < p->n[0]; ++x) {
+        long id = nid(p, x, y, z);
+        if (p->cls[id] != C_TN) continue;
+        int P[3] = {x, y, z}, X[3] = {0, 0, 0};
+        for (int a = 0; a < r->dim; ++a)
+          X[a] = c->boxed[a] ? 2 * rel_coord(p, c, a, P[a]) : 2 * P[a];
+        double f[MAXQ], rho, u[3];
+        for (int i = 0; i < q; ++i) {
+          int s[3] = {X[0] - L->xi[i][0], X[1] - L->xi[i][1], X[2] - L->xi[i][2]};
+          for (int a = 0; a < 3; ++a)
+            if (c->per[a]) s[a] = wrap(s[a], c->n[a]);
+          f[i] = c->fpost[nid(c, s[0], s[1], s[2]) * q + i];
+        }
+        moments(L, f, &rho, u);
+        for (int a = 0; a < 3; ++a) p->vel[id * 3 + a] = u[a];
+      }
+  for (int z = 0; z < p->n[2]; ++z)
+    for (int y = 0; y < p->n[1]; ++y)
+      for (int x = 0; x < p->n[0]; ++x) {
+        long id = nid(p, x, y, z);
+        long k = c->hidx[id];
+        if (k < 0) continue;
+        strain_fd(r, p, x, y, z, c->hists + ((size_t)2 * c->K + k) * 6);
+      }
+}
+
+/* Sec. 4.4, both fine sub-steps: the boundary nodes of a child level take
+ * the parent strain rate, interpolated in time (eq. TempInt) and space
+ * (eq. spaceInt) like the populations, rescaled by eq. PijResc
+ * (S^f = S^c / 2), and collide with it. */
+static void collide_boundary_hrr(orc_run* r, int l, const double* wt) {
+  level_t* c = &r->lev[l];
+  const level_t* p = &r->lev[l - 1];
+  const int q = r->L.q;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < c->n[2]; ++z)
+    for (int y = 0; y < c->n[1]; ++y)
+      for (int x = 0; x < c->n[0]; ++x) {
+        long id = nid(c, x, y, z);
+        if (c->cls[id] != C_BOUND) continue;
+        int X[3] = {x, y, z};
+        int odd[2], nodd = 0;
+        for (int a = 0; a < r->dim; ++a)
+          if (X[a] & 1) odd[nodd++] = a;
+        double S6[6] = {0, 0, 0, 0, 0, 0};
+        int n0 = nodd >= 1 ? 4 : 1, n1 = nodd >= 2 ? 4 : 1;
+        for (int s0 = 0; s0 < n0; ++s0)
+          for (int s1 = 0; s1 < n1; ++s1) {
+            int Xc[3] = {X[0], X[1], X[2]};
+            double w = 1.0;
+            if (nodd >= 1) {
+              Xc[odd[0]] = X[odd[0]] - 3 + 2 * s0;
+              w *= SPACE_W[s0];
+            }
+            if (nodd >= 2) {
+              Xc[odd[1]] = X[odd[1]] - 3 + 2 * s1;
+              w *= SPACE_W[s1];
+            }
+            int P[3];
+            for (int a = 0; a < 3; ++a)
+              P[a] = (a < r->dim) ? parent_coord(p, c, a, Xc[a]) : 0;
+            long k = c->hidx[nid(p, P[0], P[1], P[2])];
+            if (k < 0) abort();
+            for (int j = 0; j < 6; ++j) {
+              double v = 0.0;
+              for (int t = 0; t < 3; ++t) v += wt[t] * c->hists[((size_t)t * c->K + k) * 6 + j];
+              S6[j] += w * v;
+            }
+          }
+        for (int j = 0; j < 6; ++j) S6[j] *= 0.5; /* eq. PijResc */
+        memcpy(c->sused + id * 6, S6, sizeof(S6));
+        collide_hrr_lat(&r->L, c->tau, r->sigma, c->fpre + id * q, S6, c->fpost + id * q);
+      }
+}
+
+static void advance_hrr(orc_run* r, int l, const double* wt, int first_substep) {
+  level_t* v = &r->lev[l];
+  stream_level(r, v);
+  if (l >= 1) rebuild_boundary(r, l, wt);
+  velocity_field(r, v);
+  if (l + 1 < r->nlev) {
+    level_t* c = &r->lev[l + 1];
+    capture_history(r, l);
+    memcpy(c->hists, c->hists + (size_t)c->K * 6, sizeof(double) * c->K * 6);
+    memcpy(c->hists + (size_t)c->K * 6, c->hists + (size_t)2 * c->K * 6,
+           sizeof(double) * c->K * 6);
+    double wA[3], wB[3] = {0.0, 0.0, 1.0};
+    time_weights(v->nsteps == 0, wA);
+    advance_hrr(r, l + 1, wA, 1);
+    advance_hrr(r, l + 1, wB, 0);
+    restrict_tn(r, l);
+    /* TN nodes: velocity of the rebuilt state, strain rate 2 S^f of the
+     * co-located child node (eq. PijResc) */
+    const int q = r->L.q;
+    for (int z = 0; z < v->n[2]; ++z)
+      for (int y = 0; y < v->n[1]; ++y)
+        for (int x = 0; x < v->n[0]; ++x) {
+          long id = nid(v, x, y, z);
+          if (v->cls[id] != C_TN) continue;
+          double rho, u[3];
+          moments(&r->L, v->fpre + id * q, &rho, u);
+          for (int a = 0; a < 3; ++a) v->vel[id * 3 + a] = u[a];
+          int P[3] = {x, y, z}, X[3] = {0, 0, 0};
+          for (int a = 0; a < r->dim; ++a)
+            X[a] = c->boxed[a] ? 2 * rel_coord(v, c, a, P[a]) : 2 * P[a];
+          const double* sf = c->sused + nid(c, X[0], X[1], X[2]) * 6;
+          for (int j = 0; j < 6; ++j) v->sgiven[id * 6 + j] = 2.0 * sf[j];
+        }
+  }
+  collide_interior_hrr(r, v);
+  if (l >= 1) {
+    if (first_substep) parent_strain(r, l - 1);
+    collide_boundary_hrr(r, l, wt);
+  }
+  v->nsteps++;
+}
+
 static void advance(orc_run* r, int l, const double* wt) {
   level_t* v = &r->lev[l];
   stream_level(r, v);
@@ -760,7 +1037,18 @@ static void advance(orc_run* r, int l, const double* wt) {
 }
 
 int orc_step(orc_run* r, int n) {
-  for (int s = 0; s < n; ++s) advance(r, 0, NULL);
+  for (int s = 0; s < n; ++s) {
+    if (r->coll == 3)
+      advance_hrr(r, 0, NULL, 0);
+    else
+      advance(r, 0, NULL);
+  }
+  return 0;
+}
+
+int orc_set_sigma(orc_run* r, double sigma) {
+  if (!(sigma >= 0.0 && sigma <= 1.0)) return -1;
+  r->sigma = sigma;
   return 0;
 }
 

@@ -17,7 +17,8 @@
  *               1 = D3Q19, 2 = D3Q27 (generated from their definitions);
  *   - collisions: 0 = BGK (eq. BGKmodel), 1 = projected regularized (REG,
  *                 eqs. reguProcedure..LBMscheme_reg), 2 = recursive
- *                 regularized (RR, eqs. f1RR, a13RR);
+ *                 regularized (RR, eqs. f1RR, a13RR), 3 = hybrid recursive
+ *                 regularized (H-RR, eq. a1ij_HRR; Sec. 4.4 step list);
  *   - a level's nodes are numbered x fastest, then y, then z;
  *   - level 0 is periodic on every axis; level l >= 1 is described by a
  *     closed box [lo, hi] in level l-1 node units.  An axis whose box spans
@@ -48,6 +49,11 @@ void orc_a1(int lattice, const double* f, double* a1);
  * LBMscheme_reg with f1RR / reguProceduref1N). */
 void orc_collide(int lattice, int collision, double tau, const double* f_in,
                  double* f_out);
+
+/* Hybrid recursive regularized collision (collision 3; Sec. 3.3) with a
+ * given strain rate S6 = (xx, yy, zz, xy, xz, yz). */
+void orc_collide_hrr(int lattice, double tau, double sigma, const double* f_in,
+                     const double* S6, double* f_out);
 
 /* Interface weights, exposed so tests can check them against polynomials.
  * time: value at t+1/2 from values at t-1, t, t+1 (eq. TempInt); first=1
@@ -81,6 +87,8 @@ int orc_step(orc_run* r, int n);
 int orc_macros(const orc_run* r, int level, double* rho, double* u);
 /* Post-collision populations of a level, [q][N]. */
 int orc_populations(const orc_run* r, int level, double* f);
+/* Hybrid weight sigma of eq. a1ij_HRR for collision 3 (default 1). */
+int orc_set_sigma(orc_run* r, double sigma);
 /* Set the worker thread count (0 = OpenMP default); returns the count used. */
 int orc_set_threads(int n);
 

@@ -3,14 +3,14 @@
 //   k_stream_collide  fused stream + collide of every active node of a level
 //                     (eq. LBMequation), in place with the AA pattern;
 //   k_capture         parent pre-collision (drho, u, f^(1)) at t+1 on a child
-//                     box surface -> three-slot history (steps 2a/2b, 2g);
+//                     box surface -> three-slot history;
 //   k_inject          child TF / IE nodes: temporal (eq. TempInt) and spatial
 //                     (eq. spaceInt) interpolation staged per face tile in
 //                     shared memory, rescaling (eq. rescff), written where
 //                     the child's next update reads them;
 //   k_restrict        parent TN nodes: filtered child f^(1) (eq. filterFneq),
 //                     rescaling (eq. rescfc), written where the parent's next
-//                     update reads them (step 3d);
+//                     update reads them (the restriction);
 //   k_init / k_macros / k_diag_* / k_probe   set-up and read-out.
 //
 // AA pattern.  A step of parity 0 reads g_i of node n from plane i at n and

@@ -5,16 +5,17 @@
 // Schedule of one step of level l (parent of level l+1), issued as kernels:
 //   [l >= 1] K3 inject level l's TF/IE nodes from its parent's history;
 //   [child]  K2 record level l's pre-collision state at t+1 on the child box
-//            surface (steps 2a/2b/2g need it before the fine sub-steps);
+//            surface (the fine sub-steps interpolate from it);
 //            advance(l+1) with the temporal weights of eq. TempInt (t+1/2);
 //            K4 restrict the child's pre-collision state at its t+1 into
-//            level l's TN nodes (step 3d) -- it only needs the child's state
+//            level l's TN nodes (the restriction) -- it only needs the child's state
 //            after its first sub-step, which already determines it;
 //            advance(l+1) with the direct transfer (t+1);
-//   K1 stream + collide level l (steps 2a + 3e for the coarse level).
+//   K1 stream + collide level l (the coarse streaming of the asynchronous
+//      iteration and the coarse collision of the synchronous one).
 // The coarse level therefore streams and collides in one fused pass after
-// the fine sub-steps, as step 2a / step 3e allow: nothing it streams is
-// changed by the fine sub-steps except its TN nodes, which step 3d rebuilds.
+// the fine sub-steps: nothing it streams is changed by the fine sub-steps
+// except its TN nodes, which the restriction rebuilds anyway.
 #include <cuda_runtime.h>
 
 #include <algorithm>

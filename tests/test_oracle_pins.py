@@ -483,3 +483,210 @@ def test_reflected_acoustic_wave_order_of_magnitude():
     ratio = refl / inc
     assert 1.0 / 6000 < ratio < 3.0 / 2000, 1 / ratio
     assert abs(out["BGK"][2] - out["RR"][2]) < 1e-3 * out["RR"][2]
+
+
+# ------------------------------------------- hybrid recursive regularized
+
+def test_hrr_collision_closed_form():
+    """eq. a1ij_HRR at one node: the post-collision off-equilibrium second
+    moment is (1 - 1/tau) [sigma a1 + (1 - sigma)(-2 tau rho cs^2 S)]; mass
+    and momentum are conserved; sigma = 1 is the RR collision exactly."""
+    rng = np.random.default_rng(11)
+    for lat in LATS:
+        for sigma in (0.0, 0.3, 0.995):
+            f = _random_state(rng, lat)
+            S6 = 1e-3 * rng.standard_normal(6)
+            if lat == "D2Q9":
+                S6[[2, 4, 5]] = 0.0
+            tau = 0.57
+            out = oracle.collide_hrr(lat, tau, sigma, f, S6)
+            xi, _ = oracle.lattice(lat)
+            rho = f.sum()
+            u = (xi.T @ f) / rho
+            assert abs(out.sum() - rho) < 1e-15
+            np.testing.assert_allclose(xi.T @ out, xi.T @ f, atol=1e-15)
+            fe = oracle.feq(lat, rho, u)
+            S = np.array([[S6[0], S6[3], S6[4]], [S6[3], S6[1], S6[5]], [S6[4], S6[5], S6[2]]])
+            want = (1 - 1 / tau) * (sigma * oracle.a1(lat, f)
+                                    + (1 - sigma) * (-2 * tau * rho * CS2 * S))
+            got = np.einsum("ia,ib,i->ab", xi.astype(float), xi.astype(float), out - fe)
+            dim = 2 if lat == "D2Q9" else 3
+            np.testing.assert_allclose(got[:dim, :dim], want[:dim, :dim], atol=1e-14)
+        np.testing.assert_allclose(oracle.collide_hrr(lat, 0.57, 1.0, f, S6),
+                                   oracle.collide(lat, "RR", 0.57, f), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("mk", [lambda: W.small_2level_2d("RR"),
+                                lambda: W.small_3d("D3Q19", nlevels=2)],
+                         ids=["2d", "3d"])
+def test_hrr_sigma_one_reproduces_rr_on_levels(mk):
+    """With sigma = 1 the finite-difference strain (and with it every strain
+    transfer of Sec. 4.4) drops out: the hybrid run equals the RR run on every
+    level to round-off."""
+    case = mk()
+    a = oracle.Run.from_case(case)
+    b = oracle.Run.from_case(case.with_(collision="HRR"), sigma=1.0)
+    a.step(4)
+    b.step(4)
+    for l in range(case.nlevels):
+        ra, ua = a.macros(l)
+        rb, ub = b.macros(l)
+        m = ~np.isnan(ra)
+        assert np.max(np.abs(ra[m] - rb[m])) < 1e-13
+        assert np.max(np.abs(ua[:, m] - ub[:, m])) < 1e-13
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q19"])
+@pytest.mark.parametrize("sigma", [0.995, 0.5, 0.0])
+def test_hrr_shear_viscosity(lat, sigma):
+    """The finite-difference strain of eq. stressT carries the same viscosity
+    as the projected one (Chapman-Enskog link, eq. linkTauNu): a shear wave
+    decays at nu = cs^2 (tau - 1/2) for any sigma; sigma = 0 adds only the
+    O(k^2) truncation of the central difference (about 1% at 128 nodes a
+    wavelength, tau = 0.55)."""
+    L = 128
+    dims = (L, 2, 1) if lat == "D2Q9" else (L, 2, 2)
+    for tau in (0.55, 0.6):
+        c = W.Case("shear", lat, "HRR", tau, dims, [],
+                   dict(kind="shear", axis=0, comp=1, amplitude=1e-4), 0)
+        r = oracle.Run.from_case(c, sigma=sigma)
+        X, _, _ = W.level_coords(c, 0)
+        a0 = _amp_sin(r.macros(0)[1][1], X, L)
+        T = 1600
+        r.step(T)
+        a1 = _amp_sin(r.macros(0)[1][1], X, L)
+        nu_meas = -math.log(a1 / a0) / (T * (2 * math.pi / L) ** 2)
+        nu = CS2 * (tau - 0.5)
+        assert abs(nu_meas / nu - 1) < 0.015, (tau, nu_meas, nu)
+
+
+def _hrr_spectrum(sigma, k, nu=1e-6, mach=0.1, h=1e-7):
+    """Eigenvalues of the one-step map of a plane perturbation exp(i k x) of
+    the uniform D2Q9 state (rho0 = 1, u = Ma cs e_x): the linearised H-RR
+    collision (Jacobian of the oracle's collision in f and in the strain, by
+    central differences) with the strain of the perturbation from the
+    centred difference i sin(k), followed by streaming exp(-i k xi_x)."""
+    xi, _ = oracle.lattice("D2Q9")
+    tau = 0.5 + nu / CS2
+    ub = np.array([mach * W.CS, 0.0, 0.0])
+    fb = oracle.feq("D2Q9", 1.0, ub)
+    z6 = np.zeros(6)
+    Jf = np.zeros((9, 9))
+    JS = np.zeros((9, 6))
+    for j in range(9):
+        e = np.zeros(9)
+        e[j] = h
+        Jf[:, j] = (oracle.collide_hrr("D2Q9", tau, sigma, fb + e, z6)
+                    - oracle.collide_hrr("D2Q9", tau, sigma, fb - e, z6)) / (2 * h)
+    for j in range(6):
+        e = np.zeros(6)
+        e[j] = h
+        JS[:, j] = (oracle.collide_hrr("D2Q9", tau, sigma, fb, e)
+                    - oracle.collide_hrr("D2Q9", tau, sigma, fb, -e)) / (2 * h)
+    du = np.vstack([xi[:, 0] - ub[0], xi[:, 1] - ub[1]])  # d u / d f at rho0 = 1
+    Sm = np.zeros((6, 9), complex)
+    Sm[0] = 1j * math.sin(k) * du[0]
+    Sm[3] = 0.5j * math.sin(k) * du[1]
+    M = np.diag(np.exp(-1j * k * xi[:, 0])) @ (Jf + JS @ Sm)
+    return np.linalg.eigvals(M)
+
+
+def test_hrr_spurious_acoustic_mode_damping():
+    """Linear stability (Sec. 5.3): the spuriousAc mode (eigenvalue near -1,
+    i.e. omega_r ~ pi) is damped by the RR collision as a mode of viscosity
+    nu, and by H-RR as one of viscosity nu + (1 - sigma) cs^2 / 4 (eq.
+    tauSpuriousAc), 418 nu for nu = 1e-6, sigma = 0.995.  The physical
+    acoustic and shear modes keep the RR damping."""
+    nu = 1e-6
+    k = 0.05
+
+    def split(lam):
+        damp = -np.log(np.abs(lam))
+        spurious = np.abs(np.abs(np.angle(lam)) - math.pi) < 0.2
+        return damp, spurious
+
+    d1, s1 = split(_hrr_spectrum(1.0, k, nu))
+    d2, s2 = split(_hrr_spectrum(0.995, k, nu))
+    # RR: the least damped mode near omega_r = pi decays like a mode of
+    # viscosity nu through the collision's factor (1 - 1/tau): 4 nu / cs^2
+    ac1 = np.min(d1[s1])
+    assert abs(ac1 / (4 * nu / CS2) - 1) < 0.02, ac1
+    ac2 = np.min(d2[s2])
+    want = (nu + (1 - 0.995) * CS2 / 4) / nu
+    assert abs((ac2 / ac1) / want - 1) < 0.03, (ac2 / ac1, want)
+    assert abs(want - 418) < 1
+    # hydrodynamic modes (|omega_r| small, at nu = 1e-3 where nu k^2 stands
+    # well above the differentiation error): the isothermal Navier-Stokes
+    # damping nu k^2 of the shear and both acoustic waves (bulk viscosity
+    # 2 nu / d, d = 2), and the same with sigma = 0.995 to 1%
+    nu, k = 1e-3, 0.2
+    hyd = []
+    for sigma in (1.0, 0.995):
+        lam = _hrr_spectrum(sigma, k, nu, h=1e-6)
+        d = -np.log(np.abs(lam[np.abs(np.angle(lam)) < 0.5])) / (nu * k * k)
+        hyd.append(np.sort(d[d < 10]))
+    assert hyd[0].size == hyd[1].size == 3
+    np.testing.assert_allclose(hyd[0], 1.0, rtol=0.03)
+    np.testing.assert_allclose(hyd[1], hyd[0], rtol=0.01)
+
+
+@pytest.mark.parametrize("case", list(_layouts())[:3], ids=lambda c: c.name)
+def test_hrr_rest_and_uniform_flow_exact(case):
+    """A uniform state has zero strain and zero f^(1): the hybrid collision
+    and the strain transfers of Sec. 4.4 leave it unchanged on every level."""
+    U0 = (0.1 * W.CS, 0.04 * W.CS, 0.02 * W.CS if case.dim == 3 else 0.0)
+    c = case.with_(collision="HRR", ic=dict(kind="uniform", u0=U0, drho=0.003))
+    r = oracle.Run.from_case(c, sigma=0.5)
+    r.step(6 if case.dim == 3 else 20)
+    for l in range(r.nlevels):
+        rho, u = r.macros(l)
+        m = ~np.isnan(rho)
+        assert np.max(np.abs(rho[m] - 1.003)) < 1e-13
+        np.testing.assert_allclose(u[:, m], np.repeat(np.asarray(U0)[:, None], m.sum(), 1),
+                                   atol=1e-14)
+
+
+def test_hrr_shear_wave_along_interface_two_levels():
+    """The Sec. 4.4 strain transfers (S^f = S^c / 2 at the fine outer layer,
+    2 S^f at the coarse ring) are consistent: a shear wave parallel to the
+    interface decays at the coarse rate nu_c k^2 on both levels with sigma =
+    0.5, as with the RR collision."""
+    Lx, Ly = 32, 64
+    tau = 0.6
+    c = W.Case("shear2l", "D2Q9", "HRR", tau, (Lx, Ly, 1), [((8, 0, 0), (24, Ly, 1))],
+               dict(kind="shear", axis=1, comp=0, amplitude=1e-4), 0)
+    r = oracle.Run.from_case(c, sigma=0.5)
+    T = 200
+    r.step(T)
+    k = 2 * math.pi / Ly
+    want = 1e-4 * math.exp(-CS2 * (tau - 0.5) * k * k * T)
+    for l in range(2):
+        rho, u = r.macros(l)
+        X, Y, _ = W.level_coords(c, l)
+        n = r.dims(l)[0]
+        m = ~np.isnan(rho).reshape(n[1], n[0])
+        ux = u[0].reshape(n[1], n[0])
+        for j in range(n[1]):
+            assert np.ptp(ux[j][m[j]]) < 2e-3 * 1e-4
+        col = ux[:, np.nonzero(m[0])[0][0]]
+        a = _amp_sin(col, Y.reshape(n[1], n[0])[:, 0], Ly)
+        assert abs(a / want - 1) < 0.015, (l, a, want)
+
+
+def test_hrr_reflected_acoustic_wave_like_rr():
+    """The acoustic reflection where the convected pulse of Sec. 9.2 leaves
+    the fine level does not come from the non-hydrodynamic modes, so H-RR
+    with sigma = 0.995 reflects the same wave as RR (Sec. 9.2, H-RR run)."""
+    out = {}
+    for coll, sigma in (("RR", None), ("HRR", 0.995)):
+        case = e5_case(coll)
+        r = oracle.Run(case.lattice, case.collision, case.tau0, case.dims, case.boxes)
+        if sigma is not None:
+            r.set_sigma(sigma)
+        for l in range(2):
+            r.init_level(l, *e5_fields(case, l))
+        r.init_done()
+        r.step(case.steps)
+        out[coll] = e5_ratio(r.macros(0)[0], r.macros(1)[0], case)
+    assert out["HRR"][1] == out["RR"][1] and out["HRR"][3] == out["RR"][3]
+    assert abs(out["HRR"][2] / out["RR"][2] - 1) < 0.01
