@@ -62,10 +62,14 @@ extern "C" {
 #define LBM_D3Q19 1
 #define LBM_D3Q27 2
 /* Collisions: eq. BGKmodel; eqs. reguProcedure..LBMscheme_reg (REG);
- * eqs. f1RR, a13RR (RR). */
+ * eqs. f1RR, a13RR (RR); hybrid recursive regularized (H-RR, eq. a1ij_HRR:
+ * a1 = sigma a1^(2) + (1 - sigma)(-2 tau rho cs^2 S), S from second-order
+ * central differences of the pre-collision velocity, with the strain-rate
+ * transfers of Sec. 4.4 at refinement interfaces). */
 #define LBM_BGK 0
 #define LBM_REG 1
 #define LBM_RR 2
+#define LBM_HRR 3
 /* Population storage: g = f - w rho0 in binary32 or binary16 (compute is
  * always binary32). */
 #define LBM_FP32_SHIFTED 0
@@ -83,7 +87,7 @@ typedef struct {
 
 typedef struct {
   int lattice;   /* LBM_D2Q9 | LBM_D3Q19 | LBM_D3Q27 */
-  int collision; /* LBM_BGK | LBM_REG | LBM_RR */
+  int collision; /* LBM_BGK | LBM_REG | LBM_RR | LBM_HRR */
   int storage;   /* LBM_FP32_SHIFTED | LBM_FP16_SHIFTED */
   double tau0;   /* level-0 relaxation time, > 1/2; level l uses
                     tau_l = 2 tau_{l-1} - 1/2 (eq. rescTau) */
@@ -99,6 +103,9 @@ typedef struct {
                       mean (free-stream) velocity keeps the stored values, and
                       their rounding, small.  |U| components <= 0.5; U_z = 0
                       for D2Q9.  Results do not depend on U beyond rounding. */
+  double sigma;  /* LBM_HRR only: hybrid weight sigma of eq. a1ij_HRR in
+                    [0, 1] (1 = RR; the paper's runs use 0.995); ignored by
+                    the other collisions */
 } lbm_config;
 
 /* Optional device allocator (e.g. a framework's caching allocator).

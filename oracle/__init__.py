@@ -165,6 +165,8 @@ class Run:
     @classmethod
     def from_case(cls, case, init=True, sigma=None):
         r = cls(case.lattice, case.collision, case.tau0, case.dims, case.boxes, case.rho0)
+        if sigma is None and case.collision == "HRR":
+            sigma = case.sigma
         if sigma is not None:
             r.set_sigma(sigma)
         if init:

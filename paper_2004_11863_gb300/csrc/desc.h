@@ -25,6 +25,14 @@ struct LevelView {
   // updated (inactive); empty when the level has no child.
   int has_ina;
   int ina_lo[3], ina_hi[3];
+  // The restriction ring and what it encloses (TN nodes = this box minus
+  // the inactive one); empty when the level has no child.
+  int has_tn;
+  int tn_lo[3], tn_hi[3];
+  // Hybrid collision on a refined level: the outer node layer (bounded
+  // axes) collides in its own kernel, after the parent's strain rate at
+  // t+1 exists.
+  int skip_bnd;
 };
 
 // Reference state of the shifted storage: level arrays hold

@@ -492,6 +492,26 @@ __global__ void __launch_bounds__(InjTile<L>::TI * InjTile<L>::TJ)
   store_pre<L, S>(fb, c.plane, ad, par, g);
 }
 
+// Strain rate S = (grad u + grad u^T) / 2 by second-order central
+// differences (hybrid collision, eq. a1ij_HRR), from the velocity deviations
+// of the two neighbours along each axis:
+// up[a][b] = du_b(x + e_a), um[a][b] = du_b(x - e_a).
+template <class L>
+__device__ __forceinline__ void strain_from(const float (&up)[3][3], const float (&um)[3][3],
+                                            float (&S)[6]) {
+  float gr[3][3];  // gr[a][b] = d_a u_b
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gr[a][b] = (a < L::D) ? 0.5f * (up[a][b] - um[a][b]) : 0.0f;
+  S[0] = gr[0][0];
+  S[1] = gr[1][1];
+  S[2] = gr[2][2];
+  S[3] = 0.5f * (gr[0][1] + gr[1][0]);
+  S[4] = 0.5f * (gr[0][2] + gr[2][0]);
+  S[5] = 0.5f * (gr[1][2] + gr[2][1]);
+}
+
 // ----------------------------------------------------------- K4: restrict
 // Parent TN nodes.  resc = 2 tau_c / tau_f (eq. rescfc); ppar / cpar: the
 // parent's and the child's next updates.  A block handles kTnPerBlock TN
@@ -499,18 +519,26 @@ __global__ void __launch_bounds__(InjTile<L>::TI * InjTile<L>::TJ)
 // the weighted f^(1) of its child node, the block sums the 3^D neighbours in
 // a fixed order (so results do not depend on scheduling), and one thread per
 // TN node rebuilds and stores the populations.
+// HRR (hybrid collision): the rebuilt TN node is collided at once with
+// S = 2 S^f (eq. PijResc), S^f from central differences of the child
+// velocities at the co-located node's axis neighbours (among the filter
+// neighbours), and its post-collision state stored for the parent's update
+// of parity ppar (which skips TN nodes); its velocity deviation goes to the
+// parent's velocity planes pdu.
 template <class L>
 struct TnShape {
   static constexpr int NB = (L::D == 3) ? 27 : 9;   // filter neighbours
   static constexpr int M = (L::D == 3) ? 8 : 16;    // TN nodes per block
 };
 
-template <class L, class S>
+template <class L, class S, bool HRR, bool MOV>
 __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
-    k_restrict(LevelView p, LevelView c, TnDesc T, float resc, int ppar, int cpar, RefF ref) {
+    k_restrict(LevelView p, LevelView c, TnDesc T, float resc, int ppar, int cpar, RefF ref,
+               float* pdu, float omega_p, float sig, float ks_p) {
   constexpr int NB = TnShape<L>::NB, M = TnShape<L>::M, Q = L::Q;
   __shared__ float red[M][NB][Q];
   __shared__ float cm[M][4];
+  __shared__ float cu[HRR ? M : 1][HRR ? NB : 1][3];
   const int kn = threadIdx.x, m = threadIdx.y;
   const long long k = (long long)blockIdx.x * M + m;
   const int run = blockIdx.y;
@@ -547,6 +575,11 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
                     (L::D == 3 ? (dz == 0 ? 0.5f : 0.25f) : 1.0f);
 #pragma unroll
     for (int i = 0; i < Q; ++i) red[m][kn][i] = w * f1[i];
+    if constexpr (HRR) {
+      cu[m][kn][0] = ux;
+      cu[m][kn][1] = uy;
+      cu[m][kn][2] = uz;
+    }
     if (dx == 0 && dy == 0 && dz == 0) {
       cm[m][0] = drho;
       cm[m][1] = ux;
@@ -571,7 +604,38 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
     });
     S* fp = static_cast<S*>(p.f) + run * p.run_stride;
     const NodeAddr a = node_addr<L>(p, P[0], P[1], P[2]);
-    store_pre<L, S>(fp, p.plane, a, ppar, g);
+    if constexpr (HRR) {
+      float up[3][3] = {}, um[3][3] = {};
+      for (int ax = 0; ax < L::D; ++ax) {
+        const int ip = 13 - (L::D == 2 ? 9 : 0) + (ax == 0 ? 1 : ax == 1 ? 3 : 9);
+        const int im = 13 - (L::D == 2 ? 9 : 0) - (ax == 0 ? 1 : ax == 1 ? 3 : 9);
+        for (int b = 0; b < 3; ++b) {
+          up[ax][b] = cu[m][ip][b];
+          um[ax][b] = cu[m][im][b];
+        }
+      }
+      HrrIn hy;
+      hy.sig = sig;
+      hy.ks = ks_p;
+      strain_from<L>(up, um, hy.s);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) hy.s[j] *= 2.0f;  // eq. PijResc
+      collide_emit<L, 3, MOV>(
+          g, omega_p, ref,
+          [&](auto I, float val) {
+            constexpr int i = decltype(I)::value;
+            if (ppar == 0)
+              Store<S>::st(fp + (long long)opp<L>(i) * p.plane + a.at(0, 0, 0), val);
+            else
+              Store<S>::st(fp + (long long)i * p.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)),
+                           val);
+          },
+          &hy);
+      float* d = pdu + (long long)run * L::D * p.plane + a.at(0, 0, 0);
+      for (int b = 0; b < L::D; ++b) d[(long long)b * p.plane] = cm[m][1 + b];
+    } else {
+      store_pre<L, S>(fp, p.plane, a, ppar, g);
+    }
   }
 }
 

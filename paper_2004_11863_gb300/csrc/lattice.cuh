@@ -348,16 +348,25 @@ __device__ __forceinline__ void deviations(const float (&g)[L::Q], const RefF& R
   duz = (L::D == 3) ? (jz - drho * R.Uz) * inv : 0.0f;
 }
 
+// Strain-rate input of the hybrid collision (eq. a1ij_HRR):
+// a1 <- sig a1 + ks rho S with ks = -2 tau cs^2 (1 - sig);
+// s = (S_xx, S_yy, S_zz, S_xy, S_xz, S_yz).
+struct HrrIn {
+  float sig, ks;
+  float s[6];
+};
+
 // Collision of shifted populations; the post-collision value of each
 // direction is handed to emit(integral_constant<i>, value) as soon as it is
 // formed, so no array of outputs (or of equilibria) stays live.
 // COLL: 0 BGK (eq. BGKmodel), 1 REG (eq. LBMscheme_reg with H^(2) only),
-// 2 RR (eqs. f1RR, a13RR).  omega = 1 - 1/tau.
+// 2 RR (eqs. f1RR, a13RR), 3 H-RR (eq. a1ij_HRR, then the RR recursion;
+// needs hy).  omega = 1 - 1/tau.
 // MOV = false: the reference velocity is zero (rest-state shift) and every
 // term in U is folded away at compile time.
 template <class L, int COLL, bool MOV, class Emit>
 __device__ __forceinline__ void collide_emit(const float (&g)[L::Q], float omega, const RefF& Rin,
-                                             Emit&& emit) {
+                                             Emit&& emit, const HrrIn* hy = nullptr) {
   // (moments, deviations and the equilibrium of each direction)
   const float Ux = MOV ? Rin.Ux : 0.0f, Uy = MOV ? Rin.Uy : 0.0f,
               Uz = (MOV && L::D == 3) ? Rin.Uz : 0.0f, rho0 = Rin.rho0;
@@ -424,8 +433,19 @@ __device__ __forceinline__ void collide_emit(const float (&g)[L::Q], float omega
       axz = (L::D == 3) ? pxz - rho * ux * uz : 0.0f;
       ayz = (L::D == 3) ? pyz - rho * uy * uz : 0.0f;
     }
+    if constexpr (COLL == 3) {
+      const float kr = hy->ks * rho;
+      axx = hy->sig * axx + kr * hy->s[0];
+      ayy = hy->sig * ayy + kr * hy->s[1];
+      axy = hy->sig * axy + kr * hy->s[3];
+      if constexpr (L::D == 3) {
+        azz = hy->sig * azz + kr * hy->s[2];
+        axz = hy->sig * axz + kr * hy->s[4];
+        ayz = hy->sig * ayz + kr * hy->s[5];
+      }
+    }
     float A[7] = {0, 0, 0, 0, 0, 0, 0};
-    if constexpr (COLL == 2) {
+    if constexpr (COLL >= 2) {
       A[XXY] = 2.0f * ux * axy + uy * axx;
       A[YYX] = 2.0f * uy * axy + ux * ayy;
       if constexpr (L::D == 3) {
@@ -461,7 +481,7 @@ __device__ __forceinline__ void collide_emit(const float (&g)[L::Q], float omega
       eq_pair(std::integral_constant<int, i>{}, xi, xj);
       const float h = h2a_of(std::integral_constant<int, i>{});
       float t = 0.0f;
-      if constexpr (COLL == 2) t = third<L, i>(A);
+      if constexpr (COLL >= 2) t = third<L, i>(A);
       emit(std::integral_constant<int, i>{}, wmul<L, i>(xi + omega * (h + t)));
       emit(std::integral_constant<int, j>{}, wmul<L, j>(xj + omega * (h - t)));
     });

@@ -66,6 +66,10 @@ struct Level {
   void* hist_mem = nullptr;
   double origin[3] = {0, 0, 0}, h = 1.0;  // node positions in level-0 units
   int head = 1;  // history slot holding the newest parent state (t+1)
+  // hybrid collision only: velocity-deviation planes [run][D][plane] and
+  // (l >= 1) the parent strain-rate history [run][3][6][K]
+  void* du_mem = nullptr;
+  void* sh_mem = nullptr;
 };
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -206,7 +210,9 @@ void release(lbm_ctx* h) {
   for (int l = 0; l < h->nlev; ++l) {
     h->dfree(h->lev[l].mem);
     h->dfree(h->lev[l].hist_mem);
-    h->lev[l].mem = h->lev[l].hist_mem = nullptr;
+    h->dfree(h->lev[l].du_mem);
+    h->dfree(h->lev[l].sh_mem);
+    h->lev[l].mem = h->lev[l].hist_mem = h->lev[l].du_mem = h->lev[l].sh_mem = nullptr;
   }
   h->dfree(h->probe_ijk);
   h->dfree(h->probe_rec);
@@ -295,6 +301,8 @@ void build_view(lbm_ctx* h, int l) {
   }
   w.batch = h->batch;
   w.has_ina = 0;
+  w.has_tn = 0;
+  w.skip_bnd = (h->cfg.collision == LBM_HRR && l >= 1) ? 1 : 0;
   v.n_nodes = (long long)v.n[0] * v.n[1] * v.n[2];
   v.n_active = v.n_nodes;
   if (l + 1 < h->nlev) {
@@ -310,6 +318,11 @@ void build_view(lbm_ctx* h, int l) {
         w.ina_hi[a] = v.n[a] - 1;
       }
       ina *= (w.ina_hi[a] - w.ina_lo[a] + 1);
+    }
+    w.has_tn = 1;
+    for (int a = 0; a < 3; ++a) {
+      w.tn_lo[a] = c.boxed[a] ? c.lo[a] + 1 : 0;
+      w.tn_hi[a] = c.boxed[a] ? c.hi[a] - 1 : v.n[a] - 1;
     }
     v.n_active = v.n_nodes - ina;
   }
@@ -404,6 +417,16 @@ void build_interface(lbm_ctx* h, int l) {
   T.count = T.start[T.nf];
 }
 
+// Device bytes of the hybrid collision's extra arrays on level l.
+size_t hrr_du_bytes(const lbm_ctx* h, int l) {
+  if (h->cfg.collision != LBM_HRR) return 0;
+  return sizeof(float) * (size_t)h->D * (size_t)h->lev[l].view.plane * h->batch;
+}
+size_t hrr_sh_bytes(const lbm_ctx* h, int l) {
+  if (h->cfg.collision != LBM_HRR || l < 1) return 0;
+  return sizeof(float) * 3 * 6 * (size_t)h->lev[l].ring.K * h->batch;
+}
+
 const float kTimeQuad[3] = {-1.0f / 8.0f, 3.0f / 4.0f, 3.0f / 8.0f};  // eq. TempInt
 const float kTimeLin[3] = {0.0f, 0.5f, 0.5f};   // first step: no t-1 yet
 const float kTimeDirect[3] = {0.0f, 0.0f, 1.0f};  // synchronous sub-step
@@ -489,6 +512,85 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
   return LBM_OK;
 }
 
+inline float hrr_ks(const lbm_ctx* h, double tau) {
+  return (float)(-2.0 * tau / 3.0 * (1.0 - h->cfg.sigma));  // -2 tau cs^2 (1 - sigma)
+}
+
+// One step of level l with its finer levels for the hybrid collision
+// (Sec. 4.4).  Differences from advance(): each update is preceded by the
+// velocity pass; the restriction collides the TN nodes itself; a refined
+// level's outer node layer collides after its update, with the parent's
+// strain rate interpolated from the strain history -- which, on the first
+// sub-step, first receives the parent's S at t+1 (that needs this level's
+// post-collision middle nodes for the TN velocities).
+// (kinds: 5 velocity, 6 parent strain, 7 outer-layer collision)
+int advance_hrr(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_before_update,
+                bool first_substep) {
+  Level& v = h->lev[l];
+  const int st = h->cfg.storage;
+  const RefState& ref = h->ref;
+  const int par = 1 - v.last;
+  const float sig = (float)h->cfg.sigma;
+  float* du = (float*)v.du_mem;
+  int slots[3] = {0, 0, 0};
+  if (l >= 1) {
+    const Level& p = h->lev[l - 1];
+    const float resc = (float)(v.tau / (2.0 * p.tau));  // eq. rescff
+    slots[0] = (v.head + 1) % 3;
+    slots[1] = (v.head + 2) % 3;
+    slots[2] = v.head;
+    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref, h->cur));
+  }
+  if (l + 1 < h->nlev) {
+    Level& c = h->lev[l + 1];
+    c.head = (c.head + 1) % 3;
+    LAUNCH_K(1, l, h->ops.capture(v.view, c.ring, st, par, 0, c.head, c.head, ref, h->cur));
+    int rc = advance_hrr(h, l + 1, v.nsteps == 0 ? kTimeLin : kTimeQuad, launch, nullptr, true);
+    if (rc) return rc;
+    cudaStream_t main = h->cur;
+    const bool fork = launch && !h->profiling;
+    if (fork) {
+      CK(cudaEventRecord(h->ev_fork[l], main));
+      CK(cudaStreamWaitEvent(h->side[l], h->ev_fork[l], 0));
+      h->cur = h->side[l];
+    }
+    const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
+    LAUNCH_K(3, l, h->ops.restrict_hrr(v.view, c.view, c.tn, st, resc, par, 1 - c.last, du,
+                                       omega_of(v.tau), sig, hrr_ks(h, v.tau), ref, h->cur));
+    if (fork) CK(cudaEventRecord(h->ev_restrict[l], h->side[l]));
+    LAUNCH_K(5, l, h->ops.velocity(v.view, st, par, du, ref, h->cur));
+    if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
+    LAUNCH_K(0, l, h->ops.stream_collide_hrr(v.view, st, par, omega_of(v.tau), du, sig,
+                                             hrr_ks(h, v.tau), ref, h->cur));
+    if (fork) {
+      CK(cudaEventRecord(h->ev_join[l], h->side[l]));
+      h->cur = main;
+    }
+    v.last = par;
+    v.nsteps++;
+    rc = advance_hrr(h, l + 1, kTimeDirect, launch, fork ? h->ev_restrict[l] : nullptr, false);
+    if (rc) return rc;
+    if (fork) CK(cudaStreamWaitEvent(main, h->ev_join[l], 0));
+  } else {
+    LAUNCH_K(5, l, h->ops.velocity(v.view, st, par, du, ref, h->cur));
+    if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
+    LAUNCH_K(0, l, h->ops.stream_collide_hrr(v.view, st, par, omega_of(v.tau), du, sig,
+                                             hrr_ks(h, v.tau), ref, h->cur));
+    v.last = par;
+    v.nsteps++;
+  }
+  if (l >= 1) {
+    Level& p = h->lev[l - 1];
+    float* sh = (float*)v.sh_mem;
+    if (first_substep)
+      LAUNCH_K(6, l - 1, h->ops.parent_strain(p.view, v.view, v.ring, v.tn, st, sh, v.head, v.head,
+                                              1 - p.last, 1 - v.last, 0, ref, h->cur));
+    LAUNCH_K(7, l, h->ops.collide_bnd(v.view, v.bnd, v.ring, st, sh, wt, slots, omega_of(v.tau),
+                                      sig, hrr_ks(h, v.tau), par, ref, h->cur));
+  }
+  return LBM_OK;
+}
+
 int probe_launch(lbm_ctx* h, bool launch) {
   if (h->probe_n <= 0) return LBM_OK;
   const Level& v = h->lev[h->probe_level];
@@ -498,7 +600,8 @@ int probe_launch(lbm_ctx* h, bool launch) {
 }
 
 int coarse_step(lbm_ctx* h, bool launch) {
-  int rc = advance(h, 0, nullptr, launch, nullptr);
+  int rc = h->cfg.collision == LBM_HRR ? advance_hrr(h, 0, nullptr, launch, nullptr, false)
+                                       : advance(h, 0, nullptr, launch, nullptr);
   if (rc) return rc;
   return probe_launch(h, launch);
 }
@@ -513,6 +616,10 @@ int seed_history(lbm_ctx* h) {
     h->lev[l].head = 1;
     LAUNCH(h->ops.capture(p.view, h->lev[l].ring, h->cfg.storage, p.last, 1, 1, 0, h->ref,
                           h->cur));
+    if (h->cfg.collision == LBM_HRR)
+      LAUNCH(h->ops.parent_strain(p.view, h->lev[l].view, h->lev[l].ring, h->lev[l].tn,
+                                  h->cfg.storage, (float*)h->lev[l].sh_mem, 1, 0, p.last,
+                                  h->lev[l].last, 1, h->ref, h->cur));
   }
   h->seeded = true;
   return LBM_OK;
@@ -558,7 +665,7 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
   if (!out) return LBM_EINVAL;
   *out = nullptr;
   if (!cfg) return LBM_EINVAL;
-  if (cfg->lattice < 0 || cfg->lattice > 2 || cfg->collision < 0 || cfg->collision > 2 ||
+  if (cfg->lattice < 0 || cfg->lattice > 2 || cfg->collision < 0 || cfg->collision > 3 ||
       cfg->storage < 0 || cfg->storage > 1 || cfg->nlevels < 1 ||
       cfg->nlevels > LBM_MAX_LEVELS || cfg->batch < 1 || !(cfg->tau0 > 0.5) ||
       !(cfg->rho0 > 0.0) || !std::isfinite(cfg->tau0))
@@ -566,6 +673,7 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(cfg->u_ref[a]) || std::fabs(cfg->u_ref[a]) > 0.5) return LBM_EINVAL;
   if (cfg->lattice == LBM_D2Q9 && cfg->u_ref[2] != 0.0) return LBM_EINVAL;
+  if (cfg->collision == LBM_HRR && !(cfg->sigma >= 0.0 && cfg->sigma <= 1.0)) return LBM_EINVAL;
   if (alloc && (!alloc->alloc || !alloc->free)) return LBM_EINVAL;
   lbm_ctx* h = new (std::nothrow) lbm_ctx();
   if (!h) return LBM_ENOMEM;
@@ -630,6 +738,25 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
       v.ring.hist = (float*)v.hist_mem;
       cudaMemsetAsync(v.hist_mem, 0, hb, h->stream);
     }
+    const size_t db = hrr_du_bytes(h, l), sb = hrr_sh_bytes(h, l);
+    if (db) {
+      v.du_mem = h->dalloc(db);
+      if (!v.du_mem) {
+        release(h);
+        delete h;
+        return LBM_ENOMEM;
+      }
+      cudaMemsetAsync(v.du_mem, 0, db, h->stream);
+    }
+    if (sb) {
+      v.sh_mem = h->dalloc(sb);
+      if (!v.sh_mem) {
+        release(h);
+        delete h;
+        return LBM_ENOMEM;
+      }
+      cudaMemsetAsync(v.sh_mem, 0, sb, h->stream);
+    }
   }
   bool ok = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   for (int l = 0; l < h->nlev && ok; ++l)
@@ -655,7 +782,8 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
 int lbm_bytes(const lbm_config* cfg, unsigned long long* bytes) {
   if (!cfg || !bytes) return LBM_EINVAL;
   if (cfg->lattice < 0 || cfg->lattice > 2 || cfg->nlevels < 1 ||
-      cfg->nlevels > LBM_MAX_LEVELS || cfg->batch < 1 || cfg->storage < 0 || cfg->storage > 1)
+      cfg->nlevels > LBM_MAX_LEVELS || cfg->batch < 1 || cfg->storage < 0 || cfg->storage > 1 ||
+      cfg->collision < 0 || cfg->collision > 3)
     return LBM_EINVAL;
   lbm_ctx* h = new (std::nothrow) lbm_ctx();
   if (!h) return LBM_ENOMEM;
@@ -671,7 +799,7 @@ int lbm_bytes(const lbm_config* cfg, unsigned long long* bytes) {
     for (int l = 0; l < h->nlev; ++l) build_view(h, l);
     for (int l = 1; l < h->nlev; ++l) build_interface(h, l);
     for (int l = 0; l < h->nlev; ++l) {
-      total += h->lev[l].bytes;
+      total += h->lev[l].bytes + hrr_du_bytes(h, l) + hrr_sh_bytes(h, l);
       if (l >= 1)
         total += sizeof(float) * 3ull * h->lev[l].ring.nv * h->lev[l].ring.K * h->batch;
     }

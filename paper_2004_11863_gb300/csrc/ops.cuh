@@ -24,6 +24,24 @@ struct Ops {
   // K4: fine -> coarse restriction.
   cudaError_t (*restrict_tn)(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
                              float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s);
+  // Hybrid collision (H-RR): velocity planes, the level update with
+  // finite-difference strain, the parent strain history, the child's outer
+  // layer collision and the restriction that collides TN nodes.
+  cudaError_t (*velocity)(const LevelView& v, int storage, int par, float* du, const RefState& ref,
+                          cudaStream_t s);
+  cudaError_t (*stream_collide_hrr)(const LevelView& v, int storage, int par, float omega,
+                                    const float* du, float sig, float ks, const RefState& ref,
+                                    cudaStream_t s);
+  cudaError_t (*parent_strain)(const LevelView& p, const LevelView& c, const RingDesc& R,
+                               const TnDesc& T, int storage, float* sh, int s_new, int s_also,
+                               int ppar, int cpar, int mode, const RefState& ref, cudaStream_t s);
+  cudaError_t (*collide_bnd)(const LevelView& c, const BndDesc& B, const RingDesc& R, int storage,
+                             const float* sh, const float* wt, const int* slots, float omega,
+                             float sig, float ks, int par, const RefState& ref, cudaStream_t s);
+  cudaError_t (*restrict_hrr)(const LevelView& p, const LevelView& c, const TnDesc& T,
+                              int storage, float resc, int ppar, int cpar, float* pdu,
+                              float omega_p, float sig, float ks_p, const RefState& ref,
+                              cudaStream_t s);
   cudaError_t (*init)(const LevelView& v, int storage, int run, const double* rho, const double* u,
                       const RefState& ref, cudaStream_t s);
   cudaError_t (*macros_d)(const LevelView& v, int storage, int run, int last, double* rho,

@@ -2,6 +2,7 @@
 // per-lattice translation units).
 #pragma once
 #include "kernels.cuh"
+#include "kernels_hrr.cuh"
 #include "ops.cuh"
 
 namespace mlbm {
@@ -123,10 +124,136 @@ cudaError_t restrict_tn(const LevelView& p, const LevelView& c, const TnDesc& T,
   if (T.count == 0) return cudaSuccess;
   dim3 block(TnShape<L>::NB, TnShape<L>::M);
   dim3 grid(blocks_for(T.count, TnShape<L>::M), p.batch);
+  const RefF R = make_ref_f<L>(ref);
   if (storage == 0)
-    k_restrict<L, float><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, make_ref_f<L>(ref));
+    k_restrict<L, float, false, false><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, R,
+                                                              nullptr, 0.0f, 1.0f, 0.0f);
   else
-    k_restrict<L, __half><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, make_ref_f<L>(ref));
+    k_restrict<L, __half, false, false><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, R,
+                                                               nullptr, 0.0f, 1.0f, 0.0f);
+  return cudaGetLastError();
+}
+
+inline bool moving(const RefState& ref) {
+  return ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
+}
+
+template <class L, class S, bool MOV>
+void restrict_hrr_t(const LevelView& p, const LevelView& c, const TnDesc& T, float resc, int ppar,
+                    int cpar, float* pdu, float omega_p, float sig, float ks_p, const RefF& R,
+                    cudaStream_t s) {
+  dim3 block(TnShape<L>::NB, TnShape<L>::M);
+  dim3 grid(blocks_for(T.count, TnShape<L>::M), p.batch);
+  k_restrict<L, S, true, MOV><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, R, pdu, omega_p,
+                                                      sig, ks_p);
+}
+
+template <class L>
+cudaError_t restrict_hrr(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
+                         float resc, int ppar, int cpar, float* pdu, float omega_p, float sig,
+                         float ks_p, const RefState& ref, cudaStream_t s) {
+  if (T.count == 0) return cudaSuccess;
+  const RefF R = make_ref_f<L>(ref);
+  const bool mov = moving(ref);
+  if (storage == 0) {
+    if (mov)
+      restrict_hrr_t<L, float, true>(p, c, T, resc, ppar, cpar, pdu, omega_p, sig, ks_p, R, s);
+    else
+      restrict_hrr_t<L, float, false>(p, c, T, resc, ppar, cpar, pdu, omega_p, sig, ks_p, R, s);
+  } else {
+    if (mov)
+      restrict_hrr_t<L, __half, true>(p, c, T, resc, ppar, cpar, pdu, omega_p, sig, ks_p, R, s);
+    else
+      restrict_hrr_t<L, __half, false>(p, c, T, resc, ppar, cpar, pdu, omega_p, sig, ks_p, R, s);
+  }
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t velocity(const LevelView& v, int storage, int par, float* du, const RefState& ref,
+                     cudaStream_t s) {
+  const long long n = (long long)v.n[0] * v.n[1] * v.n[2];
+  dim3 grid(blocks_for(n, 128), v.batch);
+  if (storage == 0)
+    k_velocity<L, float><<<grid, 128, 0, s>>>(v, du, par, make_ref_f<L>(ref));
+  else
+    k_velocity<L, __half><<<grid, 128, 0, s>>>(v, du, par, make_ref_f<L>(ref));
+  return cudaGetLastError();
+}
+
+template <class L, class S, bool MOV>
+void sc_hrr_t(const LevelView& v, int par, float omega, const float* du, float sig, float ks,
+              const RefF& R, cudaStream_t s) {
+  dim3 block(32, 4, 1);
+  dim3 grid((v.n[0] + 31) / 32, (v.n[1] + 3) / 4, v.n[2] * v.batch);
+  if (par == 0)
+    k_stream_collide_hrr<L, S, 0, MOV><<<grid, block, 0, s>>>(v, omega, R, du, sig, ks);
+  else
+    k_stream_collide_hrr<L, S, 1, MOV><<<grid, block, 0, s>>>(v, omega, R, du, sig, ks);
+}
+
+template <class L>
+cudaError_t stream_collide_hrr(const LevelView& v, int storage, int par, float omega,
+                               const float* du, float sig, float ks, const RefState& ref,
+                               cudaStream_t s) {
+  const RefF R = make_ref_f<L>(ref);
+  const bool mov = moving(ref);
+  if (storage == 0) {
+    if (mov)
+      sc_hrr_t<L, float, true>(v, par, omega, du, sig, ks, R, s);
+    else
+      sc_hrr_t<L, float, false>(v, par, omega, du, sig, ks, R, s);
+  } else {
+    if (mov)
+      sc_hrr_t<L, __half, true>(v, par, omega, du, sig, ks, R, s);
+    else
+      sc_hrr_t<L, __half, false>(v, par, omega, du, sig, ks, R, s);
+  }
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t parent_strain(const LevelView& p, const LevelView& c, const RingDesc& R,
+                          const TnDesc& T, int storage, float* sh, int s_new, int s_also, int ppar,
+                          int cpar, int mode, const RefState& ref, cudaStream_t s) {
+  if (R.K == 0) return cudaSuccess;
+  dim3 grid(blocks_for(R.K, 64), p.batch);
+  if (storage == 0)
+    k_parent_strain<L, float><<<grid, 64, 0, s>>>(p, c, R, T, sh, s_new, s_also, ppar, cpar,
+                                                  mode, make_ref_f<L>(ref));
+  else
+    k_parent_strain<L, __half><<<grid, 64, 0, s>>>(p, c, R, T, sh, s_new, s_also, ppar, cpar,
+                                                   mode, make_ref_f<L>(ref));
+  return cudaGetLastError();
+}
+
+template <class L, class S, bool MOV>
+void collide_bnd_t(const LevelView& c, const BndDesc& B, const RingDesc& R, const float* sh,
+                   const float* wt, const int* slots, float omega, float sig, float ks, int par,
+                   const RefF& ref, cudaStream_t s) {
+  dim3 grid(blocks_for(B.count, 64), c.batch);
+  k_collide_bnd<L, S, MOV><<<grid, 64, 0, s>>>(c, B, R, sh, wt[0], wt[1], wt[2], slots[0],
+                                               slots[1], slots[2], omega, sig, ks, par, ref);
+}
+
+template <class L>
+cudaError_t collide_bnd(const LevelView& c, const BndDesc& B, const RingDesc& R, int storage,
+                        const float* sh, const float* wt, const int* slots, float omega, float sig,
+                        float ks, int par, const RefState& ref, cudaStream_t s) {
+  if (B.count == 0) return cudaSuccess;
+  const RefF Rf = make_ref_f<L>(ref);
+  const bool mov = moving(ref);
+  if (storage == 0) {
+    if (mov)
+      collide_bnd_t<L, float, true>(c, B, R, sh, wt, slots, omega, sig, ks, par, Rf, s);
+    else
+      collide_bnd_t<L, float, false>(c, B, R, sh, wt, slots, omega, sig, ks, par, Rf, s);
+  } else {
+    if (mov)
+      collide_bnd_t<L, __half, true>(c, B, R, sh, wt, slots, omega, sig, ks, par, Rf, s);
+    else
+      collide_bnd_t<L, __half, false>(c, B, R, sh, wt, slots, omega, sig, ks, par, Rf, s);
+  }
   return cudaGetLastError();
 }
 
@@ -220,6 +347,11 @@ Ops make_ops() {
   o.capture = detail::capture<L>;
   o.inject = detail::inject<L>;
   o.restrict_tn = detail::restrict_tn<L>;
+  o.velocity = detail::velocity<L>;
+  o.stream_collide_hrr = detail::stream_collide_hrr<L>;
+  o.parent_strain = detail::parent_strain<L>;
+  o.collide_bnd = detail::collide_bnd<L>;
+  o.restrict_hrr = detail::restrict_hrr<L>;
   o.init = detail::init<L>;
   o.macros_d = detail::macros_d<L>;
   o.macros_f = detail::macros_f<L>;

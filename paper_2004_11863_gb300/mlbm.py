@@ -41,7 +41,7 @@ class lbm_config(ctypes.Structure):
                 ("tau0", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("dims", ctypes.c_int * 3), ("nlevels", ctypes.c_int),
                 ("box", lbm_box * (MAX_LEVELS - 1)), ("batch", ctypes.c_int),
-                ("u_ref", ctypes.c_double * 3)]
+                ("u_ref", ctypes.c_double * 3), ("sigma", ctypes.c_double)]
 
 
 class lbm_ic(ctypes.Structure):
@@ -131,7 +131,7 @@ def lbm_lattice(lattice: str):
 
 def make_config(lattice: str, collision: str, tau0: float, dims: Sequence[int], boxes,
                 storage: str = "fp32", batch: int = 1, rho0: float = 1.0,
-                u_ref=(0.0, 0.0, 0.0)) -> lbm_config:
+                u_ref=(0.0, 0.0, 0.0), sigma: float = 1.0) -> lbm_config:
     c = lbm_config()
     c.lattice = workloads.LATTICES[lattice]
     c.collision = workloads.COLLISIONS[collision]
@@ -149,13 +149,14 @@ def make_config(lattice: str, collision: str, tau0: float, dims: Sequence[int], 
     c.batch = int(batch)
     for a in range(3):
         c.u_ref[a] = float(u_ref[a])
+    c.sigma = float(sigma)
     return c
 
 
 def lbm_bytes(lattice, collision, tau0, dims, boxes, storage="fp32", batch=1, rho0=1.0,
-              u_ref=(0.0, 0.0, 0.0)) -> int:
+              u_ref=(0.0, 0.0, 0.0), sigma=1.0) -> int:
     """Device bytes a run of this layout needs (no device work)."""
-    cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0, u_ref)
+    cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0, u_ref, sigma)
     b = ctypes.c_ulonglong()
     _check(lib().lbm_bytes(ctypes.byref(cfg), ctypes.byref(b)), "lbm_bytes")
     return int(b.value)
@@ -190,9 +191,11 @@ class Lbm:
     """
 
     def __init__(self, lattice, collision, tau0, dims, boxes, storage="fp32", batch=1,
-                 rho0=1.0, stream=None, torch_allocator=False, u_ref=(0.0, 0.0, 0.0)):
+                 rho0=1.0, stream=None, torch_allocator=False, u_ref=(0.0, 0.0, 0.0),
+                 sigma=1.0):
         L = lib()
-        self.cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0, u_ref)
+        self.cfg = make_config(lattice, collision, tau0, dims, boxes, storage, batch, rho0, u_ref,
+                               sigma)
         self.lattice = lattice
         self.q = workloads.Q_OF[lattice]
         self.nlevels = self.cfg.nlevels
@@ -210,6 +213,7 @@ class Lbm:
     @classmethod
     def from_case(cls, case, storage="fp32", batch=1, init=True, **kw):
         kw.setdefault("u_ref", case.u_ref)
+        kw.setdefault("sigma", case.sigma)
         r = cls(case.lattice, case.collision, case.tau0, case.dims, case.boxes, storage, batch,
                 case.rho0, **kw)
         if init:

@@ -28,7 +28,7 @@ import numpy as np
 CS = 1.0 / math.sqrt(3.0)
 
 LATTICES = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISIONS = {"BGK": 0, "REG": 1, "RR": 2}
+COLLISIONS = {"BGK": 0, "REG": 1, "RR": 2, "HRR": 3}
 Q_OF = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 DIM_OF = {"D2Q9": 2, "D3Q19": 3, "D3Q27": 3}
 
@@ -46,6 +46,7 @@ class Case:
     ic: dict
     steps: int
     rho0: float = 1.0
+    sigma: float = 0.995  # hybrid weight, used when collision == "HRR"
 
     @property
     def u_ref(self):
