@@ -208,6 +208,11 @@ def cpu_baseline(case, budget_s=15.0):
             "sample": f"{k} coarse steps of one {case.name} run (FP64, OpenMP on {cores} threads)"}
 
 
+# kinds of the library's per-kernel timing records (lbm_profile_read)
+KERNEL_KINDS = ((0, "update"), (1, "capture"), (2, "inject"), (3, "restrict"), (5, "velocity"),
+                (6, "parent_strain"), (7, "outer_layer_collide"))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,7 +292,7 @@ def main():
     g.profile(True)
     g.step(args.steps)
     kt = {}
-    for kind, name in ((0, "update"), (1, "capture"), (2, "inject"), (3, "restrict")):
+    for kind, name in KERNEL_KINDS:
         for l in range(case.nlevels):
             t_ms, n = g.profile_read(kind, l)
             if n:
@@ -342,11 +347,13 @@ def main():
     # ---------------- variants of the same workload (same batch) ------------
     variants = {}
     for vname, st, coll in (("fp16_shifted_rr", "fp16", case.collision),
-                            ("fp32_shifted_bgk", "fp32", "BGK")):
+                            ("fp32_shifted_bgk", "fp32", "BGK"),
+                            ("fp32_shifted_hrr", "fp32", "HRR")):
         if vname.startswith(args.storage) and coll == case.collision:
             continue
         gv = mlbm.Lbm(case.lattice, coll, case.tau0, case.dims, case.boxes, storage=st,
-                      batch=batch, rho0=case.rho0, stream=stream.cuda_stream, u_ref=case.u_ref)
+                      batch=batch, rho0=case.rho0, stream=stream.cuda_stream, u_ref=case.u_ref,
+                      sigma=case.sigma)
         for l in range(case.nlevels):
             for b in range(batch):
                 gv.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
@@ -360,13 +367,29 @@ def main():
         gv.profile(True)
         gv.step(args.steps)
         vt, vn = gv.profile_read(0, dom_level)
-        gv.profile(False)
         vs = 2 if st == "fp16" else 4
-        vb = counts[dom_level] * batch * 2 * case.q * vs
+        # algorithmic bytes of the level update: q populations read and
+        # written; the hybrid update also reads the D velocity planes once
+        vb = counts[dom_level] * batch * (2 * case.q * vs + (4 * case.dim if coll == "HRR" else 0))
         variants[vname] = {"value": round(U * batch * ws * args.steps / (vms * 1e-3) / 1e6, 1),
                            "unit": "MLUPS",
                            "dominant_kernel_gbs": round(vb / (vt / vn * 1e-3) / 1e9, 1),
                            "dominant_kernel_frac": round(vb / (vt / vn * 1e-3) / 1e9 / peak, 4)}
+        if coll == "HRR":
+            # the velocity pass reads q populations and writes D planes
+            pt, pn = gv.profile_read(5, dom_level)
+            pb = counts[dom_level] * batch * (case.q * vs + 4 * case.dim)
+            tot = sum(gv.profile_read(k, l)[0] for k, _ in KERNEL_KINDS
+                      for l in range(case.nlevels))
+            variants[vname].update({
+                "sigma": case.sigma,
+                "velocity_pass_gbs": round(pb / (pt / pn * 1e-3) / 1e9, 1),
+                "velocity_pass_frac": round(pb / (pt / pn * 1e-3) / 1e9 / peak, 4),
+                "kernel_time_share": {
+                    f"{name}_L{l}": round(gv.profile_read(k, l)[0] / tot, 4)
+                    for k, name in KERNEL_KINDS for l in range(case.nlevels)
+                    if gv.profile_read(k, l)[1]}})
+        gv.profile(False)
         gv.close()
 
     # ---------------- serving: continuous batching vs one run at a time -----

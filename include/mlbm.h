@@ -269,8 +269,10 @@ int lbm_profile(lbm_handle h, int enable);
 
 /* Sum of the recorded kernel durations (ms) and their count for one kernel
  * kind (0 level update, 1 history capture, 2 coarse-to-fine rebuild,
- * 3 fine-to-coarse restriction, 4 probe sampling) on one level (-1: all
- * levels; the level is the one updated, or the parent for 1 and 3).
+ * 3 fine-to-coarse restriction, 4 probe sampling; LBM_HRR only: 5 velocity
+ * pass, 6 parent strain-rate history, 7 outer-layer collision) on one level
+ * (-1: all levels; the level is the one updated, or the parent for 1, 3
+ * and 6).
  * Synchronises. */
 int lbm_profile_read(lbm_handle h, int kind, int level, double* total_ms,
                      long long* count);

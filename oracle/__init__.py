@@ -73,6 +73,11 @@ def lib():
             L.orc_macros.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
             L.orc_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
             L.orc_set_sigma.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_sensors_enable.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double]
+            L.orc_sensors.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_ubyte), dp, dp]
+            L.orc_set_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
@@ -213,6 +218,31 @@ class Run:
         """Hybrid weight of the H-RR collision (call before init_done)."""
         if lib().orc_set_sigma(self._h, float(sigma)) != 0:
             raise ValueError("sigma must lie in [0, 1]")
+
+    def sensors_enable(self, level, eps=0.0, g_threshold=0.0):
+        """Evaluate the non-hydrodynamic mode sensors of a level from now on
+        (eps: magnitude floor of the sign tests; g_threshold: of |f1G|)."""
+        if lib().orc_sensors_enable(self._h, level, float(eps), float(g_threshold)) != 0:
+            raise ValueError("bad sensor arguments")
+
+    def sensors(self, level):
+        """Latest sensor flags [N] (bit 0 spuriousAc, 1 spuriousS, 2
+        spuriousG), div u [N] and curl u [3, N] of a level."""
+        _, N = self.dims(level)
+        fl = np.zeros(N, dtype=np.uint8)
+        dv = np.zeros(N)
+        cu = np.zeros((3, N))
+        if lib().orc_sensors(self._h, level, fl.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                             _dp(dv), _dp(cu)) != 0:
+            raise ValueError("sensors not enabled on this level")
+        return fl, dv, cu
+
+    def set_populations(self, level, f):
+        """Set a level's (post-collision) populations, f [q, N]."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _, N = self.dims(level)
+        assert f.shape == (self.q, N)
+        lib().orc_set_populations(self._h, level, _dp(f))
 
     def init_done(self):
         lib().orc_init_done(self._h)

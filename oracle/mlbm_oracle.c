@@ -364,6 +364,16 @@ typedef struct {
   double* sused;
   double* sgiven;
   double* hists;
+  /* Non-hydrodynamic mode sensors (Sec. 7), when enabled: the latest flags
+   * per node (bit 0 spuriousAc, bit 1 spuriousS, bit 2 spuriousG), the
+   * velocity divergence [N] and vorticity [N][3] of the latest iteration,
+   * and a velocity scratch field [N][3]. */
+  int sens_on;
+  double sens_eps, sens_thr;
+  unsigned char* sflag;
+  double* sdiv;
+  double* scurl;
+  double* svel;
 } level_t;
 
 struct orc_run {
@@ -407,6 +417,10 @@ int orc_set_threads(int n) {
 }
 
 static void free_level(level_t* v) {
+  free(v->sflag);
+  free(v->sdiv);
+  free(v->scurl);
+  free(v->svel);
   free(v->vel);
   free(v->sused);
   free(v->sgiven);
@@ -978,6 +992,138 @@ static void collide_boundary_hrr(orc_run* r, int l, const double* wt) {
       }
 }
 
+/* ---------------- non-hydrodynamic mode sensors (Sec. 7) ----------------- */
+
+/* Central-difference velocity gradient g[a][b] = d_a u_b of a [N][3] field. */
+static void grad_fd(const orc_run* r, const level_t* v, const double* field, int x, int y, int z,
+                    double g[3][3]) {
+  const int X[3] = {x, y, z};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) g[a][b] = 0.0;
+  for (int a = 0; a < r->dim; ++a) {
+    int P[3] = {X[0], X[1], X[2]}, M[3] = {X[0], X[1], X[2]};
+    P[a] += 1;
+    M[a] -= 1;
+    if (v->per[a]) {
+      P[a] = wrap(P[a], v->n[a]);
+      M[a] = wrap(M[a], v->n[a]);
+    }
+    const double* up = field + nid(v, P[0], P[1], P[2]) * 3;
+    const double* um = field + nid(v, M[0], M[1], M[2]) * 3;
+    for (int b = 0; b < 3; ++b) g[a][b] = 0.5 * (up[b] - um[b]);
+  }
+}
+
+/* Evaluate the three sensors of one iteration of a level from its
+ * pre-collision state (call once every active node's pre-collision state
+ * is final, just before the collision):
+ *   spuriousAc (eq. sensorSpuriousAc): div u(t-1) * div u(t) < 0;
+ *   spuriousS (eq. sensorSpuriousS): curl u(t-1) . curl u(t) < 0;
+ *   (both only where each factor's magnitude exceeds eps: at round-off
+ *   level the sign is noise; eps = 0 is the literal test)
+ *   spuriousG (eq. sensorSpuriousG): |f1G| > threshold and neither of the
+ *     two others, with f1 = f - f^(0)(rho, u) split as eq. fneqSplit into
+ *     its projection on the second-order Hermite polynomials
+ *     (eq. reguProceduref1S, w_i / (2 cs^4) H2_i : a1) and the rest f1G.
+ * Evaluated at middle nodes (the central differences need active
+ * neighbours); other nodes get no flags.  div and curl of the previous
+ * iteration are zero before the first evaluation. */
+static void sensors_level(orc_run* r, level_t* v) {
+  if (!v->sens_on) return;
+  const lattice_t* L = &r->L;
+  const int q = L->q;
+#pragma omp parallel for schedule(static)
+  for (long id = 0; id < v->N; ++id) {
+    double rho, u[3] = {0, 0, 0};
+    if (v->cls[id] != 0) moments(L, v->fpre + id * q, &rho, u);
+    for (int a = 0; a < 3; ++a) v->svel[id * 3 + a] = u[a];
+  }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < v->n[2]; ++z)
+    for (int y = 0; y < v->n[1]; ++y)
+      for (int x = 0; x < v->n[0]; ++x) {
+        const long id = nid(v, x, y, z);
+        double* cu = v->scurl + id * 3;
+        if (v->cls[id] != C_MIDDLE) {
+          v->sflag[id] = 0;
+          v->sdiv[id] = 0.0;
+          cu[0] = cu[1] = cu[2] = 0.0;
+          continue;
+        }
+        double g[3][3];
+        grad_fd(r, v, v->svel, x, y, z, g);
+        const double div = g[0][0] + g[1][1] + g[2][2];
+        const double curl[3] = {g[1][2] - g[2][1], g[2][0] - g[0][2], g[0][1] - g[1][0]};
+        const double eps = v->sens_eps;
+        const double nc0 = sqrt(cu[0] * cu[0] + cu[1] * cu[1] + cu[2] * cu[2]);
+        const double nc1 = sqrt(curl[0] * curl[0] + curl[1] * curl[1] + curl[2] * curl[2]);
+        const int ac = v->sdiv[id] * div < 0.0 && fabs(v->sdiv[id]) > eps && fabs(div) > eps;
+        const int sh = cu[0] * curl[0] + cu[1] * curl[1] + cu[2] * curl[2] < 0.0 && nc0 > eps &&
+                       nc1 > eps;
+        /* ghost part of the off-equilibrium populations */
+        const double* f = v->fpre + id * q;
+        double rho, uu[3], feq[MAXQ], a1[3][3];
+        moments(L, f, &rho, uu);
+        feq_lat(L, rho, uu, feq);
+        a1_lat(L, f, feq, a1);
+        double n2 = 0.0;
+        for (int i = 0; i < q; ++i) {
+          double h = 0.0;
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) h += h2(L->xi[i], a, b) * a1[a][b];
+          const double f1s = L->w[i] / (2.0 * CS2 * CS2) * h;
+          const double f1g = (f[i] - feq[i]) - f1s;
+          n2 += f1g * f1g;
+        }
+        const int gh = sqrt(n2) > v->sens_thr && !ac && !sh;
+        v->sflag[id] = (unsigned char)(ac | (sh << 1) | (gh << 2));
+        v->sdiv[id] = div;
+        for (int a = 0; a < 3; ++a) cu[a] = curl[a];
+      }
+}
+
+int orc_sensors_enable(orc_run* r, int level, double eps, double g_threshold) {
+  if (level < 0 || level >= r->nlev || !(g_threshold >= 0.0) || !(eps >= 0.0)) return -1;
+  level_t* v = &r->lev[level];
+  if (!v->sens_on) {
+    v->sflag = (unsigned char*)calloc((size_t)v->N, 1);
+    v->sdiv = (double*)calloc((size_t)v->N, sizeof(double));
+    v->scurl = (double*)calloc((size_t)v->N * 3, sizeof(double));
+    v->svel = (double*)calloc((size_t)v->N * 3, sizeof(double));
+    if (!v->sflag || !v->sdiv || !v->scurl || !v->svel) return -1;
+  }
+  v->sens_on = 1;
+  v->sens_eps = eps;
+  v->sens_thr = g_threshold;
+  return 0;
+}
+
+int orc_sensors(const orc_run* r, int level, unsigned char* flags, double* div, double* curl) {
+  if (level < 0 || level >= r->nlev) return -1;
+  const level_t* v = &r->lev[level];
+  if (!v->sens_on) return -1;
+  for (long id = 0; id < v->N; ++id) {
+    if (flags) flags[id] = v->sflag[id];
+    if (div) div[id] = v->sdiv[id];
+    if (curl)
+      for (int a = 0; a < 3; ++a) curl[(size_t)a * v->N + id] = v->scurl[id * 3 + a];
+  }
+  return 0;
+}
+
+int orc_set_populations(orc_run* r, int level, const double* f) {
+  if (level < 0 || level >= r->nlev) return -1;
+  level_t* v = &r->lev[level];
+  const int q = r->L.q;
+  for (long id = 0; id < v->N; ++id)
+    for (int i = 0; i < q; ++i) {
+      v->fpost[id * q + i] = f[(size_t)i * v->N + id];
+      v->fpre[id * q + i] = v->fpost[id * q + i];
+    }
+  v->nsteps = 0;
+  return 0;
+}
+
 static void advance_hrr(orc_run* r, int l, const double* wt, int first_substep) {
   level_t* v = &r->lev[l];
   stream_level(r, v);
@@ -1012,6 +1158,7 @@ static void advance_hrr(orc_run* r, int l, const double* wt, int first_substep) 
           for (int j = 0; j < 6; ++j) v->sgiven[id * 6 + j] = 2.0 * sf[j];
         }
   }
+  sensors_level(r, v);
   collide_interior_hrr(r, v);
   if (l >= 1) {
     if (first_substep) parent_strain(r, l - 1);
@@ -1032,6 +1179,7 @@ static void advance(orc_run* r, int l, const double* wt) {
     advance(r, l + 1, wB); /* synchronous sub-step: t+1/2 -> t+1 */
     restrict_tn(r, l);
   }
+  sensors_level(r, v);
   collide_level(r, v);
   v->nsteps++;
 }

@@ -89,6 +89,19 @@ int orc_macros(const orc_run* r, int level, double* rho, double* u);
 int orc_populations(const orc_run* r, int level, double* f);
 /* Hybrid weight sigma of eq. a1ij_HRR for collision 3 (default 1). */
 int orc_set_sigma(orc_run* r, double sigma);
+/* Non-hydrodynamic mode sensors of a level (Sec. 7, eqs. sensorSpuriousAc,
+ * sensorSpuriousS, sensorSpuriousG), evaluated at every later iteration of
+ * the level from its pre-collision state at middle nodes.  eps: the sign
+ * tests of the first two count only where both factors exceed eps in
+ * magnitude (0 = the paper's literal tests); g_threshold: the spuriousG
+ * sensor fires where |f1G| exceeds it (0 = the paper's "> 0").
+ * orc_sensors returns the latest flags [N] (bit 0 spuriousAc, bit 1
+ * spuriousS, bit 2 spuriousG), div u [N] and curl u [3][N] (any may be
+ * NULL).  Both return -1 on a bad argument. */
+int orc_sensors_enable(orc_run* r, int level, double eps, double g_threshold);
+int orc_sensors(const orc_run* r, int level, unsigned char* flags, double* div, double* curl);
+/* Set a level's populations directly, f [q][N] (post-collision state). */
+int orc_set_populations(orc_run* r, int level, const double* f);
 /* Set the worker thread count (0 = OpenMP default); returns the count used. */
 int orc_set_threads(int n);
 

@@ -345,7 +345,8 @@ class Lbm:
 
     def profile_read(self, kind: int, level: int = -1):
         """(total ms, launches) of one kernel kind: 0 level update,
-        1 capture, 2 inject, 3 restrict, 4 probe."""
+        1 capture, 2 inject, 3 restrict, 4 probe; hybrid collision: 5 velocity
+        pass, 6 parent strain history, 7 outer-layer collision."""
         t = ctypes.c_double()
         n = ctypes.c_longlong()
         _check(lib().lbm_profile_read(self._h, kind, level, ctypes.byref(t), ctypes.byref(n)),

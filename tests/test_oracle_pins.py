@@ -690,3 +690,116 @@ def test_hrr_reflected_acoustic_wave_like_rr():
         out[coll] = e5_ratio(r.macros(0)[0], r.macros(1)[0], case)
     assert out["HRR"][1] == out["RR"][1] and out["HRR"][3] == out["RR"][3]
     assert abs(out["HRR"][2] / out["RR"][2] - 1) < 0.01
+
+
+# ------------------------------------------- non-hydrodynamic mode sensors
+
+def _post_map_modes(coll, tau, k, mach=0.1, h=1e-7):
+    """Eigenpairs of the linearised one-step map of post-collision states
+    f_post(t+1) = C(S f_post(t)) for a plane wave exp(i k x) on D2Q9 around
+    (rho = 1, u = Ma cs e_x): C the oracle's collision (Jacobian by central
+    differences), S the streaming multiplier exp(-i k xi_x)."""
+    xi, _ = oracle.lattice("D2Q9")
+    fb = oracle.feq("D2Q9", 1.0, [mach * W.CS, 0.0, 0.0])
+    J = np.zeros((9, 9))
+    for j in range(9):
+        e = np.zeros(9)
+        e[j] = h
+        J[:, j] = (oracle.collide("D2Q9", coll, tau, fb + e)
+                   - oracle.collide("D2Q9", coll, tau, fb - e)) / (2 * h)
+    lam, V = np.linalg.eig(J @ np.diag(np.exp(-1j * k * xi[:, 0])))
+    return fb, xi, lam, V
+
+
+def _sensor_run(coll, pick, tau=0.51, L=64, m=8, steps=5, eps=1e-12, g_thr=1e-12):
+    """Seed one eigenmode (amplitude 1e-6) on a periodic single level and
+    return the fractions of nodes flagged (Ac, S, G) at each iteration."""
+    k = 2 * math.pi * m / L
+    fb, xi, lam, V = _post_map_modes(coll, tau, k)
+    j = pick(lam, V, xi)
+    v = V[:, j] / np.max(np.abs(V[:, j]))
+    x = np.arange(L)
+    fx = fb[:, None] + 1e-6 * np.real(v[:, None] * np.exp(1j * k * x[None, :]))
+    f = np.concatenate([fx, fx], axis=1)  # two identical rows (y = 0, 1)
+    r = oracle.Run("D2Q9", coll, tau, (L, 2, 1), [])
+    r.set_populations(0, f)
+    r.init_done()
+    r.sensors_enable(0, eps, g_thr)
+    out = []
+    for _ in range(steps):
+        r.step(1)
+        fl = r.sensors(0)[0]
+        out.append(((fl & 1).mean(), ((fl >> 1) & 1).mean(), ((fl >> 2) & 1).mean()))
+    return lam[j], out
+
+
+def _flipping(lam):
+    return np.abs(np.abs(np.angle(lam)) - math.pi) < 0.25
+
+
+@pytest.mark.parametrize("coll", ["BGK", "RR"])
+def test_sensor_spurious_acoustic_mode(coll):
+    """The spuriousAc eigenmode (omega_r ~ pi, carrying density and
+    longitudinal velocity) trips eq. sensorSpuriousAc at every node from the
+    second evaluation on, and neither of the two other sensors."""
+    def pick(lam, V, xi):
+        c = [abs(V[:, j].sum()) + abs(xi[:, 0] @ V[:, j]) if _flipping(lam[j]) else -1
+             for j in range(9)]
+        return int(np.argmax(c))
+    lam, out = _sensor_run(coll, pick)
+    assert _flipping(lam)
+    for ac, s, g in out[1:]:
+        assert ac == 1.0 and s == 0.0 and g == 0.0, out
+
+
+def test_sensor_spurious_shear_mode():
+    """The RR spuriousS eigenmode (omega_r ~ pi, carrying transverse
+    velocity) trips eq. sensorSpuriousS everywhere and not the Ac sensor."""
+    def pick(lam, V, xi):
+        c = [abs(xi[:, 1] @ V[:, j]) if _flipping(lam[j]) else -1 for j in range(9)]
+        return int(np.argmax(c))
+    lam, out = _sensor_run("RR", pick)
+    for ac, s, g in out[1:]:
+        assert s == 1.0 and ac == 0.0 and g == 0.0, out
+
+
+def test_sensor_ghost_mode():
+    """An RR eigenmode with omega_r ~ pi and no density or velocity content
+    (spuriousG) trips eq. sensorSpuriousG everywhere and neither other
+    sensor (its f^(1) has no second-order Hermite part, eq. fneqSplit)."""
+    def pick(lam, V, xi):
+        c = [-(abs(V[:, j].sum()) + abs(xi[:, 0] @ V[:, j]) + abs(xi[:, 1] @ V[:, j]))
+             if _flipping(lam[j]) and abs(lam[j]) > 1e-3 else -np.inf for j in range(9)]
+        return int(np.argmax(c))
+    lam, out = _sensor_run("RR", pick)
+    for ac, s, g in out:
+        assert g == 1.0 and ac == 0.0 and s == 0.0, out
+
+
+@pytest.mark.parametrize("coll", ["BGK", "RR"])
+def test_sensor_quiet_on_physical_acoustic_wave(coll):
+    """A physical acoustic eigenmode advances its phase by |arg lambda| <
+    pi/2 per step, so div u changes sign between two iterations only on a
+    fraction of about |arg lambda| / pi of the nodes, and its vorticity is
+    zero."""
+    def pick(lam, V, xi):
+        c = [abs(V[:, j].sum()) if abs(np.angle(lam[j])) < 1.0 else -1 for j in range(9)]
+        return int(np.argmax(c))
+    lam, out = _sensor_run(coll, pick)
+    bound = abs(np.angle(lam)) / math.pi + 1.0 / 8
+    assert all(ac <= bound and s == 0.0 for ac, s, _ in out), (lam, out)
+    assert np.mean([o[0] for o in out]) < 0.2
+
+
+def test_sensors_silent_on_uniform_flow_two_levels():
+    """A uniform flow has zero velocity gradient and zero f^(1) up to
+    round-off (~1e-17 here, where the literal sign tests would fire at
+    random): with a floor of 1e-15 no sensor fires on either level."""
+    case = W.small_2level_2d().with_(ic=dict(kind="uniform", u0=(0.1 * W.CS, 0.02, 0.0)))
+    r = oracle.Run.from_case(case)
+    for l in range(2):
+        r.sensors_enable(l, 1e-15, 1e-14)
+    r.step(3)
+    for l in range(2):
+        fl, dv, cu = r.sensors(l)
+        assert not fl.any() and np.abs(dv).max() < 1e-15 and np.abs(cu).max() < 1e-15
