@@ -261,6 +261,34 @@ int lbm_sync(lbm_handle h);
  * replays count every kernel node they contain). */
 long long lbm_kernel_launches(lbm_handle h);
 
+/* Non-hydrodynamic mode sensors of Sec. 7 on one level (all runs), from the
+ * next coarse step on: at every iteration of the level, from its
+ * pre-collision state at middle nodes (not inactive, not TN, not on a
+ * refined level's outer node layer),
+ *   bit 0 spuriousAc (eq. sensorSpuriousAc): div u(t-1) * div u(t) < 0,
+ *   bit 1 spuriousS (eq. sensorSpuriousS): curl u(t-1) . curl u(t) < 0,
+ *         each counted only where both factors exceed eps in magnitude
+ *         (eps = 0: the literal sign test, which round-off can trip),
+ *   bit 2 spuriousG (eq. sensorSpuriousG): |f1G| > g_threshold and neither
+ *         other bit, f1G = f^(1) minus its second-order Hermite projection
+ *         (eqs. fneqSplit, reguProceduref1S);
+ * div u and curl u by second-order central differences.  The state before
+ * the first iteration is zero (no flags).  Allocates the level's velocity
+ * planes (D binary32 planes) if the collision does not already have them,
+ * plus one plane per div / curl component, one for |f1G| and one byte
+ * plane, per run;
+ * adds a velocity pass (unless H-RR) and a sensor pass to every iteration
+ * of the level.  Calling it again changes eps and g_threshold.  Synchronises.
+ * Returns LBM_EINVAL for a negative or non-finite eps or threshold. */
+int lbm_sensors_enable(lbm_handle h, int level, double eps, double g_threshold);
+
+/* Latest sensor state of one run on one level, in node order (x fastest):
+ * flags [N], div [N], curl [3][N] (z component only in 2D) and |f1G| [N]
+ * (the quantity the spuriousG bit thresholds); any output may be NULL.
+ * LBM_ESTATE if the sensors of the level are not enabled.  Synchronises. */
+int lbm_sensors(lbm_handle h, int level, int run, unsigned char* flags, double* div,
+                double* curl, double* gnorm);
+
 /* Per-kernel timing.  lbm_profile(h, 1) clears the record and makes the
  * following lbm_step calls launch eagerly (no graph replay) with a CUDA
  * event pair around every kernel on the handle's stream; lbm_profile(h, 0)
@@ -269,8 +297,9 @@ int lbm_profile(lbm_handle h, int enable);
 
 /* Sum of the recorded kernel durations (ms) and their count for one kernel
  * kind (0 level update, 1 history capture, 2 coarse-to-fine rebuild,
- * 3 fine-to-coarse restriction, 4 probe sampling; LBM_HRR only: 5 velocity
- * pass, 6 parent strain-rate history, 7 outer-layer collision) on one level
+ * 3 fine-to-coarse restriction, 4 probe sampling, 5 velocity pass (LBM_HRR
+ * or sensors), 6 parent strain-rate history and 7 outer-layer collision
+ * (LBM_HRR), 8 sensor pass) on one level
  * (-1: all levels; the level is the one updated, or the parent for 1, 3
  * and 6).
  * Synchronises. */

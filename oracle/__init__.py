@@ -76,7 +76,7 @@ def lib():
             L.orc_sensors_enable.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_double]
             L.orc_sensors.argtypes = [ctypes.c_void_p, ctypes.c_int,
-                                      ctypes.POINTER(ctypes.c_ubyte), dp, dp]
+                                      ctypes.POINTER(ctypes.c_ubyte), dp, dp, dp]
             L.orc_set_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
             L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -225,17 +225,18 @@ class Run:
         if lib().orc_sensors_enable(self._h, level, float(eps), float(g_threshold)) != 0:
             raise ValueError("bad sensor arguments")
 
-    def sensors(self, level):
+    def sensors(self, level, with_gnorm=False):
         """Latest sensor flags [N] (bit 0 spuriousAc, 1 spuriousS, 2
-        spuriousG), div u [N] and curl u [3, N] of a level."""
+        spuriousG), div u [N] and curl u [3, N] of a level (and |f1G| [N])."""
         _, N = self.dims(level)
         fl = np.zeros(N, dtype=np.uint8)
         dv = np.zeros(N)
         cu = np.zeros((3, N))
+        gn = np.zeros(N)
         if lib().orc_sensors(self._h, level, fl.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
-                             _dp(dv), _dp(cu)) != 0:
+                             _dp(dv), _dp(cu), _dp(gn)) != 0:
             raise ValueError("sensors not enabled on this level")
-        return fl, dv, cu
+        return (fl, dv, cu, gn) if with_gnorm else (fl, dv, cu)
 
     def set_populations(self, level, f):
         """Set a level's (post-collision) populations, f [q, N]."""

@@ -371,6 +371,7 @@ typedef struct {
   int sens_on;
   double sens_eps, sens_thr;
   unsigned char* sflag;
+  double* sgn; /* |f1G| [N] */
   double* sdiv;
   double* scurl;
   double* svel;
@@ -418,6 +419,7 @@ int orc_set_threads(int n) {
 
 static void free_level(level_t* v) {
   free(v->sflag);
+  free(v->sgn);
   free(v->sdiv);
   free(v->scurl);
   free(v->svel);
@@ -1046,6 +1048,7 @@ static void sensors_level(orc_run* r, level_t* v) {
         double* cu = v->scurl + id * 3;
         if (v->cls[id] != C_MIDDLE) {
           v->sflag[id] = 0;
+          v->sgn[id] = 0.0;
           v->sdiv[id] = 0.0;
           cu[0] = cu[1] = cu[2] = 0.0;
           continue;
@@ -1077,6 +1080,7 @@ static void sensors_level(orc_run* r, level_t* v) {
         }
         const int gh = sqrt(n2) > v->sens_thr && !ac && !sh;
         v->sflag[id] = (unsigned char)(ac | (sh << 1) | (gh << 2));
+        v->sgn[id] = sqrt(n2);
         v->sdiv[id] = div;
         for (int a = 0; a < 3; ++a) cu[a] = curl[a];
       }
@@ -1087,10 +1091,11 @@ int orc_sensors_enable(orc_run* r, int level, double eps, double g_threshold) {
   level_t* v = &r->lev[level];
   if (!v->sens_on) {
     v->sflag = (unsigned char*)calloc((size_t)v->N, 1);
+    v->sgn = (double*)calloc((size_t)v->N, sizeof(double));
     v->sdiv = (double*)calloc((size_t)v->N, sizeof(double));
     v->scurl = (double*)calloc((size_t)v->N * 3, sizeof(double));
     v->svel = (double*)calloc((size_t)v->N * 3, sizeof(double));
-    if (!v->sflag || !v->sdiv || !v->scurl || !v->svel) return -1;
+    if (!v->sflag || !v->sgn || !v->sdiv || !v->scurl || !v->svel) return -1;
   }
   v->sens_on = 1;
   v->sens_eps = eps;
@@ -1098,13 +1103,15 @@ int orc_sensors_enable(orc_run* r, int level, double eps, double g_threshold) {
   return 0;
 }
 
-int orc_sensors(const orc_run* r, int level, unsigned char* flags, double* div, double* curl) {
+int orc_sensors(const orc_run* r, int level, unsigned char* flags, double* div, double* curl,
+                double* gnorm) {
   if (level < 0 || level >= r->nlev) return -1;
   const level_t* v = &r->lev[level];
   if (!v->sens_on) return -1;
   for (long id = 0; id < v->N; ++id) {
     if (flags) flags[id] = v->sflag[id];
     if (div) div[id] = v->sdiv[id];
+    if (gnorm) gnorm[id] = v->sgn[id];
     if (curl)
       for (int a = 0; a < 3; ++a) curl[(size_t)a * v->N + id] = v->scurl[id * 3 + a];
   }

@@ -96,10 +96,11 @@ int orc_set_sigma(orc_run* r, double sigma);
  * magnitude (0 = the paper's literal tests); g_threshold: the spuriousG
  * sensor fires where |f1G| exceeds it (0 = the paper's "> 0").
  * orc_sensors returns the latest flags [N] (bit 0 spuriousAc, bit 1
- * spuriousS, bit 2 spuriousG), div u [N] and curl u [3][N] (any may be
- * NULL).  Both return -1 on a bad argument. */
+ * spuriousS, bit 2 spuriousG), div u [N], curl u [3][N] and |f1G| [N] (any
+ * may be NULL).  Both return -1 on a bad argument. */
 int orc_sensors_enable(orc_run* r, int level, double eps, double g_threshold);
-int orc_sensors(const orc_run* r, int level, unsigned char* flags, double* div, double* curl);
+int orc_sensors(const orc_run* r, int level, unsigned char* flags, double* div, double* curl,
+                double* gnorm);
 /* Set a level's populations directly, f [q][N] (post-collision state). */
 int orc_set_populations(orc_run* r, int level, const double* f);
 /* Set the worker thread count (0 = OpenMP default); returns the count used. */

@@ -29,10 +29,24 @@ struct LevelView {
   // the inactive one); empty when the level has no child.
   int has_tn;
   int tn_lo[3], tn_hi[3];
-  // Hybrid collision on a refined level: the outer node layer (bounded
-  // axes) collides in its own kernel, after the parent's strain rate at
-  // t+1 exists.
-  int skip_bnd;
+  // Hybrid collision: TN nodes are collided by the restriction and, on a
+  // refined level, the outer node layer (bounded axes) in its own kernel,
+  // after the parent's strain rate at t+1 exists.
+  int hrr;
+};
+
+// Non-hydrodynamic mode sensor state of one level (Sec. 7), laid out like
+// the population planes: div[run * plane + e], curl[(run * nc + c) * plane
+// + e] (nc = 1 in 2D, 3 in 3D), gn, flag[run * plane + e] (bit 0 spuriousAc,
+// bit 1 spuriousS, bit 2 spuriousG).  eps: magnitude floor of the sign
+// tests; g2: squared threshold of |f1G|.
+struct SensorState {
+  float* div;
+  float* curl;
+  float* gn;  // |f1G|, gn[run * plane + e]
+  unsigned char* flag;
+  int nc;
+  float eps, g2;
 };
 
 // Reference state of the shifted storage: level arrays hold

@@ -35,8 +35,16 @@ __device__ __forceinline__ bool tn_node(const LevelView& v, int x, int y, int z)
 }
 
 template <class L>
+__device__ __forceinline__ bool outer_geom(const LevelView& v, int x, int y, int z) {
+  bool b = (!v.per[0] && (x == 0 || x == v.n[0] - 1)) ||
+           (!v.per[1] && (y == 0 || y == v.n[1] - 1));
+  if constexpr (L::D == 3) b = b || (!v.per[2] && (z == 0 || z == v.n[2] - 1));
+  return b;
+}
+
+template <class L>
 __device__ __forceinline__ bool outer_layer(const LevelView& v, int x, int y, int z) {
-  if (!v.skip_bnd) return false;
+  if (!v.hrr) return false;
   bool b = (!v.per[0] && (x == 0 || x == v.n[0] - 1)) ||
            (!v.per[1] && (y == 0 || y == v.n[1] - 1));
   if constexpr (L::D == 3) b = b || (!v.per[2] && (z == 0 || z == v.n[2] - 1));
@@ -54,13 +62,15 @@ __device__ __forceinline__ void store_post_i(S* f, long long plane, const NodeAd
 }
 
 // --------------------------------------------------------------- velocity
+// (hybrid collision: TN nodes are left to the restriction, which writes
+// their velocity; otherwise every active node)
 template <class L, class S>
 __global__ void k_velocity(LevelView v, float* du, int par, RefF ref) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int run = blockIdx.y;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
-  if (inactive(v, x, y, z) || tn_node(v, x, y, z)) return;
+  if (inactive(v, x, y, z) || (v.hrr && tn_node(v, x, y, z))) return;
   const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q], drho, u[3];

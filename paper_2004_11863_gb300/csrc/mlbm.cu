@@ -70,6 +70,10 @@ struct Level {
   // (l >= 1) the parent strain-rate history [run][3][6][K]
   void* du_mem = nullptr;
   void* sh_mem = nullptr;
+  // non-hydrodynamic mode sensors (lbm_sensors_enable)
+  bool sens_on = false;
+  void* sens_mem = nullptr;
+  SensorState sens{};
 };
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -212,7 +216,9 @@ void release(lbm_ctx* h) {
     h->dfree(h->lev[l].hist_mem);
     h->dfree(h->lev[l].du_mem);
     h->dfree(h->lev[l].sh_mem);
+    h->dfree(h->lev[l].sens_mem);
     h->lev[l].mem = h->lev[l].hist_mem = h->lev[l].du_mem = h->lev[l].sh_mem = nullptr;
+    h->lev[l].sens_mem = nullptr;
   }
   h->dfree(h->probe_ijk);
   h->dfree(h->probe_rec);
@@ -302,7 +308,7 @@ void build_view(lbm_ctx* h, int l) {
   w.batch = h->batch;
   w.has_ina = 0;
   w.has_tn = 0;
-  w.skip_bnd = (h->cfg.collision == LBM_HRR && l >= 1) ? 1 : 0;
+  w.hrr = h->cfg.collision == LBM_HRR ? 1 : 0;
   v.n_nodes = (long long)v.n[0] * v.n[1] * v.n[2];
   v.n_active = v.n_nodes;
   if (l + 1 < h->nlev) {
@@ -417,10 +423,13 @@ void build_interface(lbm_ctx* h, int l) {
   T.count = T.start[T.nf];
 }
 
-// Device bytes of the hybrid collision's extra arrays on level l.
-size_t hrr_du_bytes(const lbm_ctx* h, int l) {
-  if (h->cfg.collision != LBM_HRR) return 0;
+// Device bytes of the velocity planes of level l, and of the hybrid
+// collision's extra arrays.
+size_t du_bytes(const lbm_ctx* h, int l) {
   return sizeof(float) * (size_t)h->D * (size_t)h->lev[l].view.plane * h->batch;
+}
+size_t hrr_du_bytes(const lbm_ctx* h, int l) {
+  return h->cfg.collision == LBM_HRR ? du_bytes(h, l) : 0;
 }
 size_t hrr_sh_bytes(const lbm_ctx* h, int l) {
   if (h->cfg.collision != LBM_HRR || l < 1) return 0;
@@ -454,6 +463,18 @@ inline float omega_of(double tau) { return (float)(1.0 - 1.0 / tau); }
     }                                                                    \
   } while (0)
 #define LAUNCH(expr) LAUNCH_K(-1, -1, expr)
+
+// Sensors of level l for the update of parity par, once its pre-collision
+// state is final (kind 8; with_velocity: issue the velocity pass first,
+// which the hybrid schedule has already done).
+int sensor_pass(lbm_ctx* h, int l, int par, bool launch, bool with_velocity) {
+  Level& v = h->lev[l];
+  if (!v.sens_on) return LBM_OK;
+  float* du = (float*)v.du_mem;
+  if (with_velocity) LAUNCH_K(5, l, h->ops.velocity(v.view, h->cfg.storage, par, du, h->ref, h->cur));
+  LAUNCH_K(8, l, h->ops.sensors(v.view, h->cfg.storage, du, par, v.sens, h->ref, h->cur));
+  return LBM_OK;
+}
 
 // One step of level l with its finer levels (see the file comment).
 int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_before_update) {
@@ -489,6 +510,8 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
     LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref, h->cur));
     if (fork) CK(cudaEventRecord(h->ev_restrict[l], h->side[l]));
+    int rs = sensor_pass(h, l, par, launch, true);
+    if (rs) return rs;
     // (this level may itself be a second sub-step whose update must wait
     // for its parent's restriction)
     if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
@@ -505,6 +528,8 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     if (fork) CK(cudaStreamWaitEvent(main, h->ev_join[l], 0));
     return LBM_OK;
   }
+  int rs = sensor_pass(h, l, par, launch, true);
+  if (rs) return rs;
   if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
   LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref, h->cur));
   v.last = par;
@@ -559,6 +584,8 @@ int advance_hrr(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wai
                                        omega_of(v.tau), sig, hrr_ks(h, v.tau), ref, h->cur));
     if (fork) CK(cudaEventRecord(h->ev_restrict[l], h->side[l]));
     LAUNCH_K(5, l, h->ops.velocity(v.view, st, par, du, ref, h->cur));
+    rc = sensor_pass(h, l, par, launch, false);
+    if (rc) return rc;
     if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
     LAUNCH_K(0, l, h->ops.stream_collide_hrr(v.view, st, par, omega_of(v.tau), du, sig,
                                              hrr_ks(h, v.tau), ref, h->cur));
@@ -573,6 +600,8 @@ int advance_hrr(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wai
     if (fork) CK(cudaStreamWaitEvent(main, h->ev_join[l], 0));
   } else {
     LAUNCH_K(5, l, h->ops.velocity(v.view, st, par, du, ref, h->cur));
+    int rs = sensor_pass(h, l, par, launch, false);
+    if (rs) return rs;
     if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
     LAUNCH_K(0, l, h->ops.stream_collide_hrr(v.view, st, par, omega_of(v.tau), du, sig,
                                              hrr_ks(h, v.tau), ref, h->cur));
@@ -1039,6 +1068,66 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
   h->dfree(d);
   if (e != cudaSuccess) {
     snprintf(g_errmsg, sizeof(g_errmsg), "macros: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+int lbm_sensors_enable(lbm_handle h, int level, double eps, double g_threshold) {
+  if (!h || level < 0 || level >= h->nlev || !(eps >= 0.0) || !(g_threshold >= 0.0) ||
+      !std::isfinite(eps) || !std::isfinite(g_threshold))
+    return LBM_EINVAL;
+  Level& v = h->lev[level];
+  CK(cudaStreamSynchronize(h->stream));
+  if (!v.du_mem) {
+    v.du_mem = h->dalloc(du_bytes(h, level));
+    if (!v.du_mem) return LBM_ENOMEM;
+    CK(cudaMemsetAsync(v.du_mem, 0, du_bytes(h, level), h->stream));
+  }
+  const int nc = h->D == 3 ? 3 : 1;
+  const size_t plane = (size_t)v.view.plane * h->batch;
+  if (!v.sens_mem) {
+    const size_t bytes = sizeof(float) * (2 + nc) * plane + plane;
+    v.sens_mem = h->dalloc(bytes);
+    if (!v.sens_mem) return LBM_ENOMEM;
+    CK(cudaMemsetAsync(v.sens_mem, 0, bytes, h->stream));
+    v.sens.div = (float*)v.sens_mem;
+    v.sens.curl = v.sens.div + plane;
+    v.sens.gn = v.sens.curl + nc * plane;
+    v.sens.flag = (unsigned char*)(v.sens.gn + plane);
+    v.sens.nc = nc;
+  }
+  v.sens.eps = (float)eps;
+  v.sens.g2 = (float)(g_threshold * g_threshold);
+  v.sens_on = true;
+  drop_graphs(h);  // the next coarse step captures the sensor pass
+  CK(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_sensors(lbm_handle h, int level, int run, unsigned char* flags, double* div,
+                double* curl, double* gnorm) {
+  if (!h || level < 0 || level >= h->nlev || run < 0 || run >= h->batch) return LBM_EINVAL;
+  const Level& v = h->lev[level];
+  if (!v.sens_on) return LBM_ESTATE;
+  const long long N = v.n_nodes;
+  char* d = (char*)h->dalloc(sizeof(double) * 5 * N + N);
+  if (!d) return LBM_ENOMEM;
+  double* dd = (double*)d;
+  unsigned char* df = (unsigned char*)(dd + 5 * N);
+  cudaError_t e = h->ops.sensor_read(v.view, run, v.sens, df, dd, dd + N, dd + 4 * N, h->stream);
+  ++h->launches;
+  if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, df, N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && div)
+    e = cudaMemcpyAsync(div, dd, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && curl)
+    e = cudaMemcpyAsync(curl, dd + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && gnorm)
+    e = cudaMemcpyAsync(gnorm, dd + 4 * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->dfree(d);
+  if (e != cudaSuccess) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "sensors: %s", cudaGetErrorString(e));
     return LBM_ECUDA;
   }
   return LBM_OK;

@@ -42,6 +42,13 @@ struct Ops {
                               int storage, float resc, int ppar, int cpar, float* pdu,
                               float omega_p, float sig, float ks_p, const RefState& ref,
                               cudaStream_t s);
+  // Non-hydrodynamic mode sensors (after the velocity pass) and their
+  // compact read-out.
+  cudaError_t (*sensors)(const LevelView& v, int storage, const float* du, int par,
+                         const SensorState& st, const RefState& ref, cudaStream_t s);
+  cudaError_t (*sensor_read)(const LevelView& v, int run, const SensorState& st,
+                             unsigned char* flags, double* div, double* curl, double* gnorm,
+                             cudaStream_t s);
   cudaError_t (*init)(const LevelView& v, int storage, int run, const double* rho, const double* u,
                       const RefState& ref, cudaStream_t s);
   cudaError_t (*macros_d)(const LevelView& v, int storage, int run, int last, double* rho,

@@ -3,6 +3,7 @@
 #pragma once
 #include "kernels.cuh"
 #include "kernels_hrr.cuh"
+#include "kernels_sensor.cuh"
 #include "ops.cuh"
 
 namespace mlbm {
@@ -227,6 +228,26 @@ cudaError_t parent_strain(const LevelView& p, const LevelView& c, const RingDesc
   return cudaGetLastError();
 }
 
+template <class L>
+cudaError_t sensors(const LevelView& v, int storage, const float* du, int par,
+                    const SensorState& st, const RefState& ref, cudaStream_t s) {
+  const long long n = (long long)v.n[0] * v.n[1] * v.n[2];
+  dim3 grid(blocks_for(n, 128), v.batch);
+  if (storage == 0)
+    k_sensors<L, float><<<grid, 128, 0, s>>>(v, du, par, st, make_ref_f<L>(ref));
+  else
+    k_sensors<L, __half><<<grid, 128, 0, s>>>(v, du, par, st, make_ref_f<L>(ref));
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t sensor_read(const LevelView& v, int run, const SensorState& st, unsigned char* flags,
+                        double* div, double* curl, double* gnorm, cudaStream_t s) {
+  const long long n = (long long)v.n[0] * v.n[1] * v.n[2];
+  k_sensor_read<L><<<blocks_for(n, 128), 128, 0, s>>>(v, run, st, flags, div, curl, gnorm);
+  return cudaGetLastError();
+}
+
 template <class L, class S, bool MOV>
 void collide_bnd_t(const LevelView& c, const BndDesc& B, const RingDesc& R, const float* sh,
                    const float* wt, const int* slots, float omega, float sig, float ks, int par,
@@ -352,6 +373,8 @@ Ops make_ops() {
   o.parent_strain = detail::parent_strain<L>;
   o.collide_bnd = detail::collide_bnd<L>;
   o.restrict_hrr = detail::restrict_hrr<L>;
+  o.sensors = detail::sensors<L>;
+  o.sensor_read = detail::sensor_read<L>;
   o.init = detail::init<L>;
   o.macros_d = detail::macros_d<L>;
   o.macros_f = detail::macros_f<L>;

@@ -86,6 +86,9 @@ def lib():
     L.lbm_macros.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
     L.lbm_macros_device.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     L.lbm_populations.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
+    L.lbm_sensors_enable.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.lbm_sensors.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte), dp,
+                              dp, dp]
     L.lbm_lattice.argtypes = [ctypes.c_int, ip, dp]
     L.lbm_probe_add.argtypes = [P, ctypes.c_int, ctypes.c_int, ip]
     L.lbm_probe.argtypes = [P, dp, ctypes.c_int, ip]
@@ -281,6 +284,26 @@ class Lbm:
         u = np.empty((3, N))
         _check(lib().lbm_macros(self._h, level, run, _dp(rho), _dp(u)), "lbm_macros")
         return rho, u
+
+    def sensors_enable(self, level, eps=0.0, g_threshold=0.0):
+        """lbm_sensors_enable: evaluate the non-hydrodynamic mode sensors of a
+        level at every iteration from the next coarse step on."""
+        _check(lib().lbm_sensors_enable(self._h, level, float(eps), float(g_threshold)),
+               "lbm_sensors_enable")
+
+    def sensors(self, level, run=0, with_gnorm=False):
+        """lbm_sensors: (flags [N] uint8, div [N], curl [3, N]) of a level
+        (and |f1G| [N])."""
+        N = int(np.prod(self.level_info(level)[0]))
+        fl = np.zeros(N, dtype=np.uint8)
+        dv = np.zeros(N)
+        cu = np.zeros((3, N))
+        gn = np.zeros(N)
+        dptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().lbm_sensors(self._h, level, run,
+                                 fl.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                 dptr(dv), dptr(cu), dptr(gn)), "lbm_sensors")
+        return (fl, dv, cu, gn) if with_gnorm else (fl, dv, cu)
 
     def macros_device(self, level, rho_ptr, u_ptr, run=0):
         _check(lib().lbm_macros_device(self._h, level, run, ctypes.c_void_p(rho_ptr),
