@@ -157,6 +157,28 @@ def initial_fields(case: Case, level: int):
         L = case.dims[ax]
         rho = np.full(N, rho0)
         u[comp] += U * np.sin(2.0 * np.pi * coord / L)
+    elif kind == "vortex_exp":
+        # barotropic vortex of eq. init_COVO: exponential density
+        xc, yc = ic["center"][0], ic["center"][1]
+        R, eps = ic["radius"], ic["eps"]
+        dx = _min_image(X - xc, case.dims[0])
+        dy = _min_image(Y - yc, case.dims[1])
+        g = np.exp(-(dx * dx + dy * dy) / (2.0 * R * R))
+        rho = rho0 * np.exp(-eps * eps / (2.0 * CS * CS) * g * g)
+        u[0] += -eps * (dy / R) * g
+        u[1] += eps * (dx / R) * g
+    elif kind == "shear_gauss":
+        # plane shear wave of eq. init_ShearW: u_y = U_y exp(-(x - xc)^2 / (2 R^2))
+        g = np.exp(-_min_image(X - ic["xc"], case.dims[0]) ** 2 / (2.0 * ic["radius"] ** 2))
+        rho = np.full(N, rho0)
+        u[1] += ic["amplitude"] * g
+    elif kind == "acoustic_gauss":
+        # plane acoustic wave of eq. init_Pulse, travelling in -x relative to
+        # the flow: rho' = rho0 A exp(-(x - xc)^2 / (2 R^2)), u_x = U_x - rho'/rho0 cs
+        g = np.exp(-_min_image(X - ic["xc"], case.dims[0]) ** 2 / (2.0 * ic["radius"] ** 2))
+        rp = rho0 * ic["amplitude"] * g
+        rho = rho0 + rp
+        u[0] -= rp / rho0 * CS
     elif kind == "random":
         rng = np.random.default_rng(ic["seed"])
         rho = rho0 + ic.get("drho", 1e-3) * rng.standard_normal(N)
@@ -168,6 +190,52 @@ def initial_fields(case: Case, level: int):
     if case.dim == 2:
         u[2] = 0.0
     return rho, u
+
+
+# --------------------------------------------------------------------------
+# Validation setups of Sec. 9 and 10 (quasi-1D waves and the convected
+# vortex), with periodic domains long enough that nothing that leaves the
+# region of interest comes back within the measured window (the paper
+# extends its domains with absorbing zones instead).  All in coarse units.
+# --------------------------------------------------------------------------
+
+def e4_shear_wave(collision: str = "RR", sigma: float = 0.995) -> Case:
+    """Convected shear wave (Sec. 9.1, eqs. init_ShearW, init_ShearW2):
+    U_x = U_y = 0.1 cs, R = 5, x_c = 150, nu = 1e-6; fine level on
+    0 < x < 250, coarse elsewhere; 4 cells across (periodic), 1000 long."""
+    return Case("e4_shear", "D2Q9", collision, 0.5 + 3e-6, (1000, 4, 1),
+                [((0, 0, 0), (250, 4, 1))],
+                dict(kind="shear_gauss", u0=(0.1 * CS, 0.0, 0.0), xc=150.0, radius=5.0,
+                     amplitude=0.1 * CS), 2900, sigma=sigma)
+
+
+def e5_acoustic_wave(collision: str = "RR", sigma: float = 0.995, length: int = 4000) -> Case:
+    """Convected acoustic wave (Sec. 9.2, eqs. init_Pulse, init_Pulse2):
+    A = 1e-4, R = 5, x_c = 750, U_x = 0.1 cs, nu = 1e-6; fine level on
+    500 < x < 1000; 4 cells across (periodic), `length` long."""
+    return Case("e5_acoustic", "D2Q9", collision, 0.5 + 3e-6, (length, 4, 1),
+                [((500, 0, 0), (1000, 4, 1))],
+                dict(kind="acoustic_gauss", u0=(0.1 * CS, 0.0, 0.0), xc=750.0, radius=5.0,
+                     amplitude=1e-4), 2620, sigma=sigma)
+
+
+def e6_vortex(collision: str = "RR", sigma: float = 0.995, nu: float = 1e-6,
+              height: int = 1200, length: int = 1200) -> Case:
+    """Convected barotropic vortex (Sec. 10, eqs. init_COVO, init_COVO2):
+    U_x = 0.1 cs, eps = 0.15 U_x, R = 5, centre (100, 75) shifted to mid
+    height, nu as given; fine level on 0 < x < 150 over the whole height;
+    periodic `length` x `height` domain."""
+    tau = 0.5 + nu / (CS * CS)
+    return Case("e6_vortex", "D2Q9", collision, tau, (length, height, 1),
+                [((0, 0, 0), (150, height, 1))],
+                dict(kind="vortex_exp", u0=(0.1 * CS, 0.0, 0.0),
+                     center=(100.0, height / 2.0), radius=5.0, eps=0.15 * 0.1 * CS), 1100,
+                sigma=sigma)
+
+
+def e6_probe(case: Case):
+    """Probe P1 of Sec. 10 (x = 200, 50 cells off the vortex path)."""
+    return (200, int(case.ic["center"][1]) + 50, 0)
 
 
 # --------------------------------------------------------------------------
