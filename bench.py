@@ -43,18 +43,26 @@ FALLBACK_HBM_GBS = 6800.0
 # sources it was taken on; ignored once the sources change.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the fine-level
-    # update of the 33-run benchmark (parity 1: 331.6 + 262.2 MB; parity 0:
-    # 331.6 + 255.0 MB); stored per run so that any batch scales it.
-    ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 590.1e6 / 33,
-                                       "src": "b284b0d61cd8aacd"},
+    # update of the 33-run benchmark (parity 1: 331.6 + 262.3 MB; parity 0:
+    # 331.6 + 255.1 MB); stored per run so that any batch scales it.
+    ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 590.2e6 / 33,
+                                       "src": "f29bec115bee9fa6"},
 }
 
 
 def kernel_source_hash() -> str:
+    """Hash of the level update's source: lattice.cuh (the collision) and the
+    level-update section of kernels.cuh (addressing helpers, launch shapes,
+    k_stream_collide).  Edits elsewhere do not void a traffic capture."""
+    csrc = os.path.join(ROOT, "paper_2004_11863_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "lattice.cuh", "ops_impl.cuh"):
-        with open(os.path.join(ROOT, "paper_2004_11863_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "lattice.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "kernels.cuh"), "r") as fh:
+        k = fh.read()
+    start = k.index("__device__ __forceinline__ int wrapi")
+    end = k.index("// (drho, du, f^(1)) of a population set")
+    h.update(k[start:end].encode())
     return h.hexdigest()[:16]
 
 
@@ -264,6 +272,8 @@ def main():
     for l in range(case.nlevels):
         for b in range(batch):
             g.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
+    # launch shapes of the level updates, chosen by the library's autotuner
+    shapes = g.autotune(reps=5)
     g.step(args.warmup)
     torch.cuda.synchronize()
     if ws > 1:
@@ -357,6 +367,7 @@ def main():
         for l in range(case.nlevels):
             for b in range(batch):
                 gv.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
+        gv.autotune(reps=5)
         gv.step(args.warmup)
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -427,6 +438,7 @@ def main():
                                + (f"x{case.dims[2]}" if case.dim == 3 else "")
                                + f", tau_c={case.tau0}, {args.storage}-shifted storage",
                    "batch_per_gpu": batch, "updates_per_coarse_step_per_run": U,
+                   "update_block_shapes": [f"{bx}x{by}" for bx, by in shapes],
                    "active_nodes_per_level": counts,
                    "l2": f"inputs larger than L2: {batch} runs x {bytes_per_run / 2 / 1e6:.1f} MB "
                          f"resident populations",

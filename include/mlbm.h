@@ -261,6 +261,21 @@ int lbm_sync(lbm_handle h);
  * replays count every kernel node they contain). */
 long long lbm_kernel_launches(lbm_handle h);
 
+/* Launch-shape autotuner.  For every level, times the level update with
+ * each candidate block shape (32x4, 32x2, 32x1, 64x2, 64x1, 128x1, 32x3
+ * threads along x by rows) on a scratch copy of the level (allocated and
+ * freed here, so the run itself is untouched), `reps` even + odd update
+ * pairs each after one warm-up pair, and keeps the fastest.  The shape
+ * changes which nodes share a block, never a node's arithmetic: results are
+ * bitwise the same for every shape.  shapes (may be NULL) receives
+ * [nlevels][2] = (bx, by).  The hybrid collision's update keeps 32x4.
+ * Synchronises; needs device memory for one level's populations. */
+int lbm_autotune(lbm_handle h, int reps, int* shapes);
+
+/* Set one level's update block shape explicitly: bx a multiple of 32,
+ * bx * by <= 128.  LBM_EINVAL otherwise.  Synchronises. */
+int lbm_set_block_shape(lbm_handle h, int level, int bx, int by);
+
 /* Non-hydrodynamic mode sensors of Sec. 7 on one level (all runs), from the
  * next coarse step on: at every iteration of the level, from its
  * pre-collision state at middle nodes (not inactive, not TN, not on a

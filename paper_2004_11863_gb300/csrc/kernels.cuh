@@ -244,15 +244,17 @@ struct StripAddr {
 
 // One thread updates NPT nodes (x, y0 .. y0+NPT-1, z); a warp covers 32
 // consecutive x of NPT rows.  All loads of the thread's nodes are issued
-// before the first collision.
+// before the first collision.  The block shape (blockDim.x a multiple of 32,
+// blockDim.x * blockDim.y <= 128) is chosen at run time (lbm_autotune); it
+// changes which nodes share a block, not any node's arithmetic.
 template <class L, int COLL, class S, int PAR, bool MOV>
 __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
                                            : (PAR == 0 ? K1Tune<L, S>::MINB_EVEN
                                                        : K1Tune<L, S>::MINB))
     k_stream_collide(LevelView v, float omega, RefF R) {
   constexpr int NPT = K1Tune<L, S>::NPT;
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y0 = (blockIdx.y * 4 + threadIdx.y) * NPT;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * NPT;
   int z = blockIdx.z, run = 0;
   if (v.batch > 1) {
     run = z / v.n[2];
@@ -382,28 +384,45 @@ __global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new,
 // Child TF / IE nodes (the outer node layer of the child box).  wt: temporal
 // weights on the history slots s_m1, s_0, s_p1 holding t-1, t, t+1;
 // resc = tau_f / (2 tau_c) (eq. rescff); par: the child's next update.
-// Organised by face tiles: a block covers TI x TJ
-// child nodes of one face of the child box; it first stages the temporally
+// Organised by face tiles: a block covers TI x TJ child nodes of one face of
+// the child box with G thread groups.  It first stages the temporally
 // interpolated parent history (eq. TempInt) of the parent nodes the tile's
-// stencils reach in shared memory, then every thread applies its spatial
-// stencil (eq. spaceInt, tensor product on face centres) from there,
-// rebuilds with eq. rescff and stores.  Each history value is read once per
-// tile instead of once per stencil use.
+// stencils reach in shared memory (all threads); then the G threads of a
+// node share its spatial stencil (eq. spaceInt, tensor product on face
+// centres), each for every G-th interpolated value; then they share its
+// rebuild (eq. rescff) and stores, each for every G-th direction.  Each
+// history value is read once per tile instead of once per stencil use, and
+// a node's serial work is split G ways (the kernel is latency-bound: a
+// surface's worth of nodes does not fill the GPU).
 template <class L>
 struct InjTile {
-  static constexpr int TI = (L::D == 3) ? 32 : 64;  // along the first tangent axis
-  static constexpr int TJ = (L::D == 3) ? 8 : 1;     // along the second
-  static constexpr int WI = TI / 2 + 5;              // parent window (stencil reach)
+  static constexpr int TI = 32;                   // along the first tangent axis
+  static constexpr int TJ = (L::D == 3) ? 4 : 1;  // along the second
+  static constexpr int G = (L::D == 3) ? 2 : 4;   // thread groups per node
+  static constexpr int WI = TI / 2 + 5;           // parent window (stencil reach)
   static constexpr int WJ = (L::D == 3) ? TJ / 2 + 5 : 1;
   static constexpr int NV = 4 + L::Q;
+  static constexpr int NT = TI * TJ * G;
 };
 
+// Write direction I into the cell an update of parity `par` reads.
+template <class L, class S, int I>
+__device__ __forceinline__ void store_pre_i(S* f, long long plane, const NodeAddr& a, int par,
+                                            float v) {
+  if (par == 0)
+    Store<S>::st(f + (long long)I * plane + a.at(0, 0, 0), v);
+  else
+    Store<S>::st(f + (long long)opp<L>(I) * plane + a.at(-L::c(I, 0), -L::c(I, 1), -L::c(I, 2)),
+                 v);
+}
+
 template <class L, class S>
-__global__ void __launch_bounds__(InjTile<L>::TI * InjTile<L>::TJ)
+__global__ void __launch_bounds__(InjTile<L>::NT)
     k_inject(LevelView c, InjDesc J, RingDesc R, float w0, float w1, float w2, int s_m1,
-                   int s_0, int s_p1, float resc, int par, RefF ref) {
+             int s_0, int s_p1, float resc, int par, RefF ref) {
   using T = InjTile<L>;
   __shared__ float sv[T::NV][T::WJ][T::WI];
+  __shared__ float res[T::NV][T::TJ][T::TI];
   const int run = blockIdx.y;
   // tile -> face, tile coordinates
   int f = 0;
@@ -413,36 +432,39 @@ __global__ void __launch_bounds__(InjTile<L>::TI * InjTile<L>::TJ)
   const int X0 = (tile % J.ntile1[f]) * T::TI;
   const int Y0 = (tile / J.ntile1[f]) * T::TJ;
   const int p0i = (X0 >> 1) - 2, p0j = (L::D == 3) ? (Y0 >> 1) - 2 : 0;
-  long long stride[3];
-  stride[0] = 1;
-  stride[1] = R.ext[f][0];
-  stride[2] = stride[1] * R.ext[f][1];
+  // per-face scalars picked without indexing local arrays
+  auto pick = [](const int (&v)[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); };
+  const long long ext0 = R.ext[f][0], ext01 = ext0 * R.ext[f][1];
+  const long long st1 = t1 == 0 ? 1 : (t1 == 1 ? ext0 : ext01);
+  const long long st2 = t2 == 0 ? 1 : (t2 == 1 ? ext0 : ext01);
+  const int bx1 = pick(R.boxed, t1), bx2 = pick(R.boxed, t2);
+  const int e1 = pick(R.ext[f], t1), e2 = pick(R.ext[f], t2);
+  const int pn1 = pick(R.pn, t1), pn2 = pick(R.pn, t2);
   const float* h = R.hist + (long long)run * 3 * R.nv * R.K;
   const long long K = R.K, nv = R.nv;
   // stage: parent window x values, interpolated in time
-  const int nthr = T::TI * T::TJ;
-  const int tid = threadIdx.y * T::TI + threadIdx.x;
+  const int tid = (threadIdx.z * T::TJ + threadIdx.y) * T::TI + threadIdx.x;
 #pragma unroll 4
-  for (int e = tid; e < T::NV * T::WJ * T::WI; e += nthr) {
+  for (int e = tid; e < T::NV * T::WJ * T::WI; e += T::NT) {
     const int pi = e % T::WI, pj = (e / T::WI) % T::WJ, vv = e / (T::WI * T::WJ);
     int ri = p0i + pi, rj = p0j + pj;  // parent coordinates relative to the box / absolute
     bool ok = true;
     long long idx = R.start[f];
     // first tangent axis
-    if (R.boxed[t1]) {
-      ok = ok && ri >= -1 && ri <= R.ext[f][t1] - 2;
-      idx += (long long)(ri + 1) * stride[t1];
+    if (bx1) {
+      ok = ok && ri >= -1 && ri <= e1 - 2;
+      idx += (long long)(ri + 1) * st1;
     } else {
-      ri = ((ri % R.pn[t1]) + R.pn[t1]) % R.pn[t1];
-      idx += (long long)ri * stride[t1];
+      ri = ((ri % pn1) + pn1) % pn1;
+      idx += (long long)ri * st1;
     }
     if (L::D == 3) {
-      if (R.boxed[t2]) {
-        ok = ok && rj >= -1 && rj <= R.ext[f][t2] - 2;
-        idx += (long long)(rj + 1) * stride[t2];
+      if (bx2) {
+        ok = ok && rj >= -1 && rj <= e2 - 2;
+        idx += (long long)(rj + 1) * st2;
       } else {
-        rj = ((rj % R.pn[t2]) + R.pn[t2]) % R.pn[t2];
-        idx += (long long)rj * stride[t2];
+        rj = ((rj % pn2) + pn2) % pn2;
+        idx += (long long)rj * st2;
       }
     }
     float val = 0.0f;
@@ -453,43 +475,56 @@ __global__ void __launch_bounds__(InjTile<L>::TI * InjTile<L>::TJ)
     sv[vv][pj][pi] = val;
   }
   __syncthreads();
-  const int xi = X0 + (int)threadIdx.x, xj = Y0 + (int)threadIdx.y;
-  if (xi >= c.n[t1] || (L::D == 3 && xj >= c.n[t2])) return;
-  int X[3];
-  X[a] = J.side[f] ? c.n[a] - 1 : 0;
-  X[t1] = xi;
-  if (L::D == 3)
-    X[t2] = xj;
-  else
-    X[2] = 0;
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int xi = X0 + tx, xj = Y0 + ty;
+  const int xa = J.side[f] ? pick(c.n, a) - 1 : 0;
+  // node coordinates: xa on the face axis, xi on t1, xj on t2 (0 in 2D)
+  const int Xn[3] = {a == 0 ? xa : (t1 == 0 ? xi : xj), a == 1 ? xa : (t1 == 1 ? xi : xj),
+                     a == 2 ? xa : (L::D == 3 ? (t1 == 2 ? xi : xj) : 0)};
+  bool live = xi < pick(c.n, t1) && (L::D == 2 || xj < pick(c.n, t2));
   // each boundary node is written by the first face (lowest axis) holding it
-  for (int b = 0; b < a; ++b)
-    if (J.boxed[b] && (X[b] == 0 || X[b] == c.n[b] - 1)) return;
-  // eq. spaceInt weights: -1/16 on the outer, 9/16 on the inner points
-  auto sw = [](int k) { return (k == 0 || k == 3) ? -1.0f / 16.0f : 9.0f / 16.0f; };
-  const bool oi = xi & 1, oj = (L::D == 3) && (xj & 1);
-  const int ni = oi ? 4 : 1, nj = oj ? 4 : 1;
-  // window index of the stencil's first point along each tangent axis
-  const int bi = (oi ? (xi - 3) / 2 : xi / 2) - p0i;
-  const int bj = (L::D == 3) ? ((oj ? (xj - 3) / 2 : xj / 2) - p0j) : 0;
-  float acc[T::NV];
 #pragma unroll
-  for (int j = 0; j < T::NV; ++j) acc[j] = 0.0f;
-  for (int sj = 0; sj < nj; ++sj)
-    for (int si = 0; si < ni; ++si) {
-      const float w = (oi ? sw(si) : 1.0f) * (oj ? sw(sj) : 1.0f);
-#pragma unroll
-      for (int j = 0; j < T::NV; ++j) acc[j] += w * sv[j][bj + sj][bi + si];
+  for (int b = 0; b < 3; ++b)
+    if (b < a && J.boxed[b] && (Xn[b] == 0 || Xn[b] == c.n[b] - 1)) live = false;
+  if (live) {
+    // eq. spaceInt weights: -1/16 on the outer, 9/16 on the inner points
+    auto sw = [](int k) { return (k == 0 || k == 3) ? -1.0f / 16.0f : 9.0f / 16.0f; };
+    const bool oi = xi & 1, oj = (L::D == 3) && (xj & 1);
+    const int ni = oi ? 4 : 1, nj = oj ? 4 : 1;
+    // window index of the stencil's first point along each tangent axis
+    const int bi = (oi ? (xi - 3) / 2 : xi / 2) - p0i;
+    const int bj = (L::D == 3) ? ((oj ? (xj - 3) / 2 : xj / 2) - p0j) : 0;
+    for (int j = tz; j < T::NV; j += T::G) {
+      float acc = 0.0f;
+      for (int sj = 0; sj < nj; ++sj)
+        for (int si = 0; si < ni; ++si) {
+          const float w = (oi ? sw(si) : 1.0f) * (oj ? sw(sj) : 1.0f);
+          acc += w * sv[j][bj + sj][bi + si];
+        }
+      res[j][ty][tx] = acc;
     }
-  float g[L::Q];
-  equilibrium_f<L>(acc[0], acc[1], acc[2], acc[3], ref, g);
+  }
+  __syncthreads();
+  if (!live) return;
+  // rebuild f = f0(rho, u) + resc f1 (eq. rescff), every G-th direction
+  const float drho = res[0][ty][tx], dux = res[1][ty][tx], duy = res[2][ty][tx];
+  const float duz = (L::D == 3) ? res[3][ty][tx] : 0.0f;
+  const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;
+  const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
+  float A[7], dA[7];
+  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, A, dA);
+  const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
+  const float rho = ref.rho0 + drho;
+  S* fb = static_cast<S*>(c.f) + run * c.run_stride;
+  const NodeAddr ad = node_addr<L>(c, Xn[0], Xn[1], Xn[2]);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    g[i] += resc * acc[4 + i];
+    if (i % T::G == tz) {
+      const float g = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
+                      resc * res[4 + i][ty][tx];
+      store_pre_i<L, S, i>(fb, c.plane, ad, par, g);
+    }
   });
-  S* fb = static_cast<S*>(c.f) + run * c.run_stride;
-  const NodeAddr ad = node_addr<L>(c, X[0], X[1], X[2]);
-  store_pre<L, S>(fb, c.plane, ad, par, g);
 }
 
 // Strain rate S = (grad u + grad u^T) / 2 by second-order central

@@ -70,6 +70,8 @@ struct Level {
   // (l >= 1) the parent strain-rate history [run][3][6][K]
   void* du_mem = nullptr;
   void* sh_mem = nullptr;
+  // block shape of the level update (lbm_autotune)
+  int k1_bx = 32, k1_by = 4;
   // non-hydrodynamic mode sensors (lbm_sensors_enable)
   bool sens_on = false;
   void* sens_mem = nullptr;
@@ -516,7 +518,7 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     // for its parent's restriction)
     if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
     LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
-                                         h->cur));
+                                         v.k1_bx, v.k1_by, h->cur));
     if (fork) {
       CK(cudaEventRecord(h->ev_join[l], h->side[l]));
       h->cur = main;
@@ -531,7 +533,8 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
   int rs = sensor_pass(h, l, par, launch, true);
   if (rs) return rs;
   if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
-  LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref, h->cur));
+  LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
+                                       v.k1_bx, v.k1_by, h->cur));
   v.last = par;
   v.nsteps++;
   return LBM_OK;
@@ -1071,6 +1074,88 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
     return LBM_ECUDA;
   }
   return LBM_OK;
+}
+
+// Candidate block shapes of the level update (threads along x, rows).
+static const int kShapes[][2] = {{32, 4}, {32, 2}, {32, 1}, {64, 2}, {64, 1}, {128, 1}, {32, 3}};
+
+int lbm_set_block_shape(lbm_handle h, int level, int bx, int by) {
+  if (!h || level < 0 || level >= h->nlev || bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128)
+    return LBM_EINVAL;
+  Level& v = h->lev[level];
+  if ((v.n[1] + by - 1) / by > 65535) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  v.k1_bx = bx;
+  v.k1_by = by;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle h, int reps, int* shapes) {
+  if (!h || reps < 1) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  const int nc = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = LBM_OK;
+  for (int l = 0; l < h->nlev && rc == LBM_OK; ++l) {
+    Level& v = h->lev[l];
+    if (h->cfg.collision == LBM_HRR) continue;  // the hybrid update has its own kernel
+    // time the update on a scratch copy of the level at rest (g = 0): the
+    // arithmetic does not depend on the values, and the run is untouched
+    void* scratch = h->dalloc(v.bytes);
+    if (!scratch) {
+      rc = LBM_ENOMEM;
+      break;
+    }
+    LevelView w = v.view;
+    w.f = scratch;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, v.bytes, h->stream);
+    float best = 1e30f;
+    int bx = v.k1_bx, by = v.k1_by;
+    const float om = omega_of(v.tau);
+    for (int k = 0; k < nc && e == cudaSuccess; ++k) {
+      const int cx = kShapes[k][0], cy = kShapes[k][1];
+      if ((v.n[1] + cy - 1) / cy > 65535) continue;
+      for (int r = 0; r < 1 + reps && e == cudaSuccess; ++r) {
+        if (r == 1) e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess)
+          e = h->ops.stream_collide(w, h->cfg.collision, h->cfg.storage, 0, om, h->ref, cx, cy,
+                                    h->stream);
+        if (e == cudaSuccess)
+          e = h->ops.stream_collide(w, h->cfg.collision, h->cfg.storage, 1, om, h->ref, cx, cy,
+                                    h->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        bx = cx;
+        by = cy;
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->dfree(scratch);
+    if (e != cudaSuccess) {
+      snprintf(g_errmsg, sizeof(g_errmsg), "autotune: %s", cudaGetErrorString(e));
+      rc = LBM_ECUDA;
+      break;
+    }
+    v.k1_bx = bx;
+    v.k1_by = by;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graphs(h);
+  if (shapes)
+    for (int l = 0; l < h->nlev; ++l) {
+      shapes[2 * l] = h->lev[l].k1_bx;
+      shapes[2 * l + 1] = h->lev[l].k1_by;
+    }
+  return rc;
 }
 
 int lbm_sensors_enable(lbm_handle h, int level, double eps, double g_threshold) {

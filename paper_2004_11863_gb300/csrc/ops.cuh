@@ -12,8 +12,9 @@ namespace mlbm {
 struct Ops {
   int q, d;
   // K1: fused stream + collide of every active node of a level.
+  // (bx, by: block shape, bx a multiple of 32, bx * by <= 128)
   cudaError_t (*stream_collide)(const LevelView& v, int coll, int storage, int par, float omega,
-                                const RefState& ref, cudaStream_t s);
+                                const RefState& ref, int bx, int by, cudaStream_t s);
   // K2: history capture (mode 0) or set-up (mode 1).
   cudaError_t (*capture)(const LevelView& p, const RingDesc& R, int storage, int par, int mode,
                          int s_new, int s_also, const RefState& ref, cudaStream_t s);

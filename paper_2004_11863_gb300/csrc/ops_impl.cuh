@@ -34,10 +34,12 @@ RefF make_ref_f(const RefState& r) {
 }
 
 template <class L, class S, int COLL>
-cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, cudaStream_t s) {
+cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx, int by,
+                      cudaStream_t s) {
   constexpr int NPT = K1Tune<L, S>::NPT;
-  dim3 block(32, 4, 1);
-  dim3 grid((v.n[0] + 31) / 32, (v.n[1] + 4 * NPT - 1) / (4 * NPT), v.n[2] * v.batch);
+  if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
+  dim3 block(bx, by, 1);
+  dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + by * NPT - 1) / (by * NPT), v.n[2] * v.batch);
   const bool mov = ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
@@ -56,19 +58,19 @@ cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& 
 
 template <class L, class S>
 cudaError_t sc_coll(const LevelView& v, int coll, int par, float omega, const RefState& ref,
-                    cudaStream_t s) {
+                    int bx, int by, cudaStream_t s) {
   switch (coll) {
-    case 0: return sc_launch<L, S, 0>(v, par, omega, ref, s);
-    case 1: return sc_launch<L, S, 1>(v, par, omega, ref, s);
-    default: return sc_launch<L, S, 2>(v, par, omega, ref, s);
+    case 0: return sc_launch<L, S, 0>(v, par, omega, ref, bx, by, s);
+    case 1: return sc_launch<L, S, 1>(v, par, omega, ref, bx, by, s);
+    default: return sc_launch<L, S, 2>(v, par, omega, ref, bx, by, s);
   }
 }
 
 template <class L>
 cudaError_t stream_collide(const LevelView& v, int coll, int storage, int par, float omega,
-                           const RefState& ref, cudaStream_t s) {
-  return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, ref, s)
-                      : sc_coll<L, __half>(v, coll, par, omega, ref, s);
+                           const RefState& ref, int bx, int by, cudaStream_t s) {
+  return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, ref, bx, by, s)
+                      : sc_coll<L, __half>(v, coll, par, omega, ref, bx, by, s);
 }
 
 template <class L>
@@ -109,7 +111,7 @@ cudaError_t inject(const LevelView& c, const BndDesc& B, const RingDesc& R, int 
     J.tstart[f + 1] = J.tstart[f] + (long long)J.ntile1[f] * J.ntile2[f];
   }
   dim3 grid((unsigned)J.tstart[J.nf], c.batch);
-  dim3 block(T::TI, T::TJ);
+  dim3 block(T::TI, T::TJ, T::G);
   if (storage == 0)
     k_inject<L, float><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0], slots[1],
                                               slots[2], resc, par, make_ref_f<L>(ref));

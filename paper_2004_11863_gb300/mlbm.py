@@ -87,6 +87,8 @@ def lib():
     L.lbm_macros_device.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     L.lbm_populations.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
     L.lbm_sensors_enable.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.lbm_autotune.argtypes = [P, ctypes.c_int, ip]
+    L.lbm_set_block_shape.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.lbm_sensors.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ubyte), dp,
                               dp, dp]
     L.lbm_lattice.argtypes = [ctypes.c_int, ip, dp]
@@ -284,6 +286,16 @@ class Lbm:
         u = np.empty((3, N))
         _check(lib().lbm_macros(self._h, level, run, _dp(rho), _dp(u)), "lbm_macros")
         return rho, u
+
+    def autotune(self, reps=5):
+        """lbm_autotune: choose each level's update block shape by timing;
+        returns [(bx, by)] per level."""
+        sh = (ctypes.c_int * (2 * self.nlevels))()
+        _check(lib().lbm_autotune(self._h, int(reps), sh), "lbm_autotune")
+        return [(sh[2 * l], sh[2 * l + 1]) for l in range(self.nlevels)]
+
+    def set_block_shape(self, level, bx, by):
+        _check(lib().lbm_set_block_shape(self._h, level, bx, by), "lbm_set_block_shape")
 
     def sensors_enable(self, level, eps=0.0, g_threshold=0.0):
         """lbm_sensors_enable: evaluate the non-hydrodynamic mode sensors of a

@@ -80,5 +80,7 @@ def test_null_arguments(lib):
     assert lib.lbm_step(None, 1) == -1
     assert lib.lbm_kernel_launches(None) == -1
     assert lib.lbm_sensors_enable(None, 0, 0.0, 0.0) == -1
+    assert lib.lbm_autotune(None, 1, None) == -1
+    assert lib.lbm_set_block_shape(None, 0, 32, 4) == -1
     assert lib.lbm_sensors(None, 0, 0, None, None, None, None) == -1
     lib.lbm_destroy(None)
