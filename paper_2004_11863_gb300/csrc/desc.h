@@ -6,16 +6,22 @@
 
 namespace mlbm {
 
-// One level's population storage: `batch` runs, each a set of q planes of
-// `plane` elements (structure of arrays), x fastest.  Node (x, y, z) sits at
-// element off + (z * SY + y) * SX + x of a plane.  Bounded axes carry a
+// One level's population storage: `batch` runs, each a set of q planes
+// (structure of arrays), x fastest.  Node (x, y, z) has index
+// e = off + (z * SY + y) * SX + x within a plane; plane i of run r holds it
+// at element (r / es) * run_stride + (r % es) + i * plane + es * e.  es = 1:
+// runs one after another.  es = 2 (binary16 storage with two or more runs):
+// runs 2p and 2p+1 interleaved element by element, so one 4-byte access
+// moves a node's population of both runs (plane and run_stride then count
+// the interleaved elements).  Bounded axes carry a
 // one-node ghost skin (x = -1 and x = n[0] on bounded x; y and z likewise);
 // periodic axes wrap.  Rows are padded to a multiple of 32 elements so that
 // node x = 0 of every row is 128-byte aligned for binary32 storage.
 struct LevelView {
   void* f;
-  long long plane;
-  long long run_stride;  // q * plane
+  long long plane;       // elements between consecutive planes of a run
+  long long run_stride;  // q * plane: elements between runs (run pairs if es = 2)
+  int es;                // element stride of consecutive nodes (1 or 2)
   long long off;
   int n[3];
   int per[3];

@@ -74,31 +74,43 @@ __device__ __forceinline__ bool inactive(const LevelView& v, int x, int y, int z
          y <= v.ina_hi[1] && z >= v.ina_lo[2] && z <= v.ina_hi[2];
 }
 
-// Pre-collision populations of node a for an update of parity PAR.
+// First element of run `run` (see LevelView for the layout).
+template <class S>
+__device__ __forceinline__ S* run_ptr(const LevelView& v, int run) {
+  return static_cast<S*>(v.f) + (long long)(run / v.es) * v.run_stride + (run % v.es);
+}
+template <class S>
+__device__ __forceinline__ const S* run_cptr(const LevelView& v, int run) {
+  return static_cast<const S*>(v.f) + (long long)(run / v.es) * v.run_stride + (run % v.es);
+}
+
+// Pre-collision populations of node a for an update of parity PAR (es: the
+// layout's element stride).
 template <class L, class S>
 __device__ __forceinline__ void load_pre(const S* f, long long plane, const NodeAddr& a, int par,
-                                         float (&g)[L::Q]) {
+                                         int es, float (&g)[L::Q]) {
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (par == 0)
-      g[i] = Store<S>::ld(f + (long long)i * plane + a.at(0, 0, 0));
+      g[i] = Store<S>::ld(f + (long long)i * plane + es * a.at(0, 0, 0));
     else
       g[i] = Store<S>::ld(f + (long long)opp<L>(i) * plane +
-                          a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
+                          es * a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
   });
 }
 
 // Write populations into the cells an update of parity `par` reads.
 template <class L, class S>
 __device__ __forceinline__ void store_pre(S* f, long long plane, const NodeAddr& a, int par,
-                                          const float (&g)[L::Q]) {
+                                          int es, const float (&g)[L::Q]) {
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (par == 0)
-      Store<S>::st(f + (long long)i * plane + a.at(0, 0, 0), g[i]);
+      Store<S>::st(f + (long long)i * plane + es * a.at(0, 0, 0), g[i]);
     else
-      Store<S>::st(f + (long long)opp<L>(i) * plane + a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)),
-                   g[i]);
+      Store<S>::st(
+          f + (long long)opp<L>(i) * plane + es * a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2)),
+          g[i]);
   });
 }
 
@@ -106,13 +118,14 @@ __device__ __forceinline__ void store_pre(S* f, long long plane, const NodeAddr&
 // (initial states are written like a parity-0 update).
 template <class L, class S>
 __device__ __forceinline__ void load_post(const S* f, long long plane, const NodeAddr& a,
-                                          int last, float (&g)[L::Q]) {
+                                          int last, int es, float (&g)[L::Q]) {
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (last == 0)
-      g[i] = Store<S>::ld(f + (long long)opp<L>(i) * plane + a.at(0, 0, 0));
+      g[i] = Store<S>::ld(f + (long long)opp<L>(i) * plane + es * a.at(0, 0, 0));
     else
-      g[i] = Store<S>::ld(f + (long long)i * plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)));
+      g[i] = Store<S>::ld(f + (long long)i * plane +
+                          es * a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)));
   });
 }
 
@@ -261,7 +274,7 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
     z -= run * v.n[2];
   }
   if (x >= v.n[0] || y0 >= v.n[1]) return;
-  S* f = static_cast<S*>(v.f) + run * v.run_stride;
+  S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
   StripAddr<NPT> a;
   const int off = (int)v.off;
 #pragma unroll
@@ -313,6 +326,79 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
   }
 }
 
+// Level update of binary16 storage with runs interleaved in pairs (es = 2):
+// one thread updates one node of runs 2p and 2p+1, moving each direction of
+// both runs with one 4-byte access (a half2 of the two runs' values); the
+// two collisions are the same arithmetic as k_stream_collide's.  The last
+// pair of an odd batch carries an unused run that stays at rest (zero
+// deviations collide to zero; no interface kernel touches it).
+template <class L>
+struct K1PairTune;
+#ifndef K1P_MINB_D2Q9
+#define K1P_MINB_D2Q9 8
+#endif
+#ifndef K1P_MINB_D3Q19
+#define K1P_MINB_D3Q19 4
+#endif
+#ifndef K1P_MINB_D3Q27
+#define K1P_MINB_D3Q27 3
+#endif
+template <>
+struct K1PairTune<D2Q9> {
+  static constexpr int MINB = K1P_MINB_D2Q9;
+};
+template <>
+struct K1PairTune<D3Q19> {
+  static constexpr int MINB = K1P_MINB_D3Q19;
+};
+template <>
+struct K1PairTune<D3Q27> {
+  static constexpr int MINB = K1P_MINB_D3Q27;
+};
+
+template <class L, int COLL, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
+    k_stream_collide_pair(LevelView v, float omega, RefF R) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int npairs = (v.batch + 1) / 2;
+  int z = blockIdx.z, pair = 0;
+  if (npairs > 1) {
+    pair = z / v.n[2];
+    z -= pair * v.n[2];
+  }
+  if (x >= v.n[0] || y >= v.n[1] || inactive(v, x, y, z)) return;
+  // half2 units: a plane is plane / 2 of them, node e sits at e
+  __half2* f = reinterpret_cast<__half2*>(static_cast<__half*>(v.f) + pair * v.run_stride);
+  const long long ph = v.plane / 2;
+  const NodeAddr a = node_addr<L>(v, x, y, z);
+  float ga[L::Q], gb[L::Q];
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    __half2 h;
+    if constexpr (PAR == 0)
+      h = f[i * ph + a.at(0, 0, 0)];
+    else
+      h = f[opp<L>(i) * ph + a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))];
+    const float2 t = __half22float2(h);
+    ga[i] = t.x;
+    gb[i] = t.y;
+  });
+  float pa[L::Q];
+  collide_emit<L, COLL, MOV>(ga, omega, R, [&](auto I, float val) {
+    constexpr int i = decltype(I)::value;
+    pa[i] = val;
+  });
+  collide_emit<L, COLL, MOV>(gb, omega, R, [&](auto I, float val) {
+    constexpr int i = decltype(I)::value;
+    const __half2 h = __floats2half2_rn(pa[i], val);
+    if constexpr (PAR == 0)
+      f[opp<L>(i) * ph + a.at(0, 0, 0)] = h;
+    else
+      f[i * ph + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))] = h;
+  });
+}
+
 // (drho, du, f^(1)) of a population set (deviations from the reference).
 template <class L>
 __device__ __forceinline__ void split_neq(const float (&g)[L::Q], const RefF& R, float& drho,
@@ -357,13 +443,13 @@ __global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new,
     if (R.pper[a]) c = ((c % R.pn[a]) + R.pn[a]) % R.pn[a];
     P[a] = c;
   }
-  const S* f = static_cast<const S*>(p.f) + run * p.run_stride;
+  const S* f = run_cptr<S>(p, run);
   const NodeAddr a = node_addr<L>(p, P[0], P[1], P[2]);
   float g[L::Q];
   if (mode == 0)
-    load_pre<L, S>(f, p.plane, a, par, g);
+    load_pre<L, S>(f, p.plane, a, par, p.es, g);
   else
-    load_post<L, S>(f, p.plane, a, par, g);
+    load_post<L, S>(f, p.plane, a, par, p.es, g);
   float drho, dux, duy, duz, f1[L::Q];
   split_neq<L>(g, ref, drho, dux, duy, duz, f1);
   const int nv = R.nv;
@@ -408,12 +494,12 @@ struct InjTile {
 // Write direction I into the cell an update of parity `par` reads.
 template <class L, class S, int I>
 __device__ __forceinline__ void store_pre_i(S* f, long long plane, const NodeAddr& a, int par,
-                                            float v) {
+                                            int es, float v) {
   if (par == 0)
-    Store<S>::st(f + (long long)I * plane + a.at(0, 0, 0), v);
+    Store<S>::st(f + (long long)I * plane + es * a.at(0, 0, 0), v);
   else
-    Store<S>::st(f + (long long)opp<L>(I) * plane + a.at(-L::c(I, 0), -L::c(I, 1), -L::c(I, 2)),
-                 v);
+    Store<S>::st(
+        f + (long long)opp<L>(I) * plane + es * a.at(-L::c(I, 0), -L::c(I, 1), -L::c(I, 2)), v);
 }
 
 template <class L, class S>
@@ -515,14 +601,14 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
   third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, A, dA);
   const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
   const float rho = ref.rho0 + drho;
-  S* fb = static_cast<S*>(c.f) + run * c.run_stride;
+  S* fb = run_ptr<S>(c, run);
   const NodeAddr ad = node_addr<L>(c, Xn[0], Xn[1], Xn[2]);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (i % T::G == tz) {
       const float g = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
                       resc * res[4 + i][ty][tx];
-      store_pre_i<L, S, i>(fb, c.plane, ad, par, g);
+      store_pre_i<L, S, i>(fb, c.plane, ad, par, c.es, g);
     }
   });
 }
@@ -601,10 +687,10 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
     if (c.per[0]) xx = wrapi(xx, c.n[0]);
     if (c.per[1]) yy = wrapi(yy, c.n[1]);
     if (L::D == 3 && c.per[2]) zz = wrapi(zz, c.n[2]);
-    const S* fcb = static_cast<const S*>(c.f) + run * c.run_stride;
+    const S* fcb = run_cptr<S>(c, run);
     const NodeAddr a = node_addr<L>(c, xx, yy, zz);
     float g[Q], f1[Q], drho, ux, uy, uz;  // (ux, uy, uz): velocity deviations
-    load_pre<L, S>(fcb, c.plane, a, cpar, g);
+    load_pre<L, S>(fcb, c.plane, a, cpar, c.es, g);
     split_neq<L>(g, ref, drho, ux, uy, uz, f1);
     const float w = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) *
                     (L::D == 3 ? (dz == 0 ? 0.5f : 0.25f) : 1.0f);
@@ -637,8 +723,9 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
       constexpr int i = decltype(I)::value;
       g[i] += resc * red[m][0][i];
     });
-    S* fp = static_cast<S*>(p.f) + run * p.run_stride;
+    S* fp = run_ptr<S>(p, run);
     const NodeAddr a = node_addr<L>(p, P[0], P[1], P[2]);
+    const int es = p.es;
     if constexpr (HRR) {
       float up[3][3] = {}, um[3][3] = {};
       for (int ax = 0; ax < L::D; ++ax) {
@@ -660,16 +747,17 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
           [&](auto I, float val) {
             constexpr int i = decltype(I)::value;
             if (ppar == 0)
-              Store<S>::st(fp + (long long)opp<L>(i) * p.plane + a.at(0, 0, 0), val);
+              Store<S>::st(fp + (long long)opp<L>(i) * p.plane + es * a.at(0, 0, 0), val);
             else
-              Store<S>::st(fp + (long long)i * p.plane + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)),
+              Store<S>::st(fp + (long long)i * p.plane +
+                               es * a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)),
                            val);
           },
           &hy);
       float* d = pdu + (long long)run * L::D * p.plane + a.at(0, 0, 0);
       for (int b = 0; b < L::D; ++b) d[(long long)b * p.plane] = cm[m][1 + b];
     } else {
-      store_pre<L, S>(fp, p.plane, a, ppar, g);
+      store_pre<L, S>(fp, p.plane, a, ppar, es, g);
     }
   }
 }
@@ -698,11 +786,11 @@ __global__ void k_init(LevelView v, int run, const double* rho, const double* u,
   double g0[L::Q];
   equilibrium_dev<L, double>(r - ref.rho0, u[t] - ref.U[0], u[N + t] - ref.U[1],
                              u[2 * N + t] - ref.U[2], ref.rho0, ref.U[0], ref.U[1], ref.U[2], g0);
-  S* f = static_cast<S*>(v.f) + run * v.run_stride;
+  S* f = run_ptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    Store<S>::st(f + (long long)opp<L>(i) * v.plane + a.at(0, 0, 0), (float)g0[i]);
+    Store<S>::st(f + (long long)opp<L>(i) * v.plane + v.es * a.at(0, 0, 0), (float)g0[i]);
   });
 }
 
@@ -730,10 +818,10 @@ __global__ void __launch_bounds__(kDiagThreads)
     }
     if (!near) {
       float ga[L::Q], gb[L::Q];
-      const S* fa = static_cast<const S*>(va.f) + run * va.run_stride;
-      const S* fb = static_cast<const S*>(vb.f) + run * vb.run_stride;
-      load_post<L, S>(fa, va.plane, node_addr<L>(va, x, y, z), last_a, ga);
-      load_post<L, S>(fb, vb.plane, node_addr<L>(vb, x, y, z), last_b, gb);
+      const S* fa = run_cptr<S>(va, run);
+      const S* fb = run_cptr<S>(vb, run);
+      load_post<L, S>(fa, va.plane, node_addr<L>(va, x, y, z), last_a, va.es, ga);
+      load_post<L, S>(fb, vb.plane, node_addr<L>(vb, x, y, z), last_b, vb.es, gb);
       double da = 0.0, db = 0.0;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
@@ -776,10 +864,10 @@ __global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, RefState 
     u[t] = u[N + t] = u[2 * N + t] = nan;
     return;
   }
-  const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+  const S* f = run_cptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
-  load_post<L, S>(f, v.plane, a, last, g);
+  load_post<L, S>(f, v.plane, a, last, v.es, g);
   // moments summed in FP64 (read-out precision): rho u = sum xi g + rho0 U
   double gd[L::Q], drho, jx, jy, jz;
 #pragma unroll
@@ -800,10 +888,10 @@ __global__ void k_populations(LevelView v, int run, int last, double* out, RefSt
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
   const long long N = (long long)v.n[0] * v.n[1] * v.n[2];
-  const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+  const S* f = run_cptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
-  load_post<L, S>(f, v.plane, a, last, g);
+  load_post<L, S>(f, v.plane, a, last, v.es, g);
   double base[L::Q];
   equilibrium_dev<L, double>(0.0, ref.U[0], ref.U[1], ref.U[2], ref.rho0, 0.0, 0.0, 0.0, base);
 #pragma unroll
@@ -820,10 +908,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(LevelView v, int 
   double s[4] = {0, 0, 0, 0};
   int x, y, z;
   if (node_of(v, t, x, y, z) && !inactive(v, x, y, z)) {
-    const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+    const S* f = run_cptr<S>(v, run);
     const NodeAddr a = node_addr<L>(v, x, y, z);
     float g[L::Q];
-    load_post<L, S>(f, v.plane, a, last, g);
+    load_post<L, S>(f, v.plane, a, last, v.es, g);
     sfor<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const double gi = (double)g[i];
@@ -860,10 +948,10 @@ __global__ void k_probe(LevelView v, int last, const int* ijk, int n, double* re
   const long long base = (long long)(slot % (unsigned long long)cap) * v.batch * n;
   for (int t = threadIdx.x; t < n * v.batch; t += blockDim.x) {
     const int run = t / n, k = t - run * n;
-    const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+    const S* f = run_cptr<S>(v, run);
     const NodeAddr a = node_addr<L>(v, ijk[3 * k], ijk[3 * k + 1], ijk[3 * k + 2]);
     float g[L::Q];
-    load_post<L, S>(f, v.plane, a, last, g);
+    load_post<L, S>(f, v.plane, a, last, v.es, g);
     double gd[L::Q], drho, jx, jy, jz;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) gd[i] = (double)g[i];

@@ -54,11 +54,11 @@ __device__ __forceinline__ bool outer_layer(const LevelView& v, int x, int y, in
 // Post-collision store of an update of parity PAR (the level update's).
 template <class L, class S, int I>
 __device__ __forceinline__ void store_post_i(S* f, long long plane, const NodeAddr& a, int par,
-                                             float val) {
+                                             int es, float val) {
   if (par == 0)
-    Store<S>::st(f + (long long)opp<L>(I) * plane + a.at(0, 0, 0), val);
+    Store<S>::st(f + (long long)opp<L>(I) * plane + es * a.at(0, 0, 0), val);
   else
-    Store<S>::st(f + (long long)I * plane + a.at(L::c(I, 0), L::c(I, 1), L::c(I, 2)), val);
+    Store<S>::st(f + (long long)I * plane + es * a.at(L::c(I, 0), L::c(I, 1), L::c(I, 2)), val);
 }
 
 // --------------------------------------------------------------- velocity
@@ -71,10 +71,10 @@ __global__ void k_velocity(LevelView v, float* du, int par, RefF ref) {
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
   if (inactive(v, x, y, z) || (v.hrr && tn_node(v, x, y, z))) return;
-  const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+  const S* f = run_cptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q], drho, u[3];
-  load_pre<L, S>(f, v.plane, a, par, g);
+  load_pre<L, S>(f, v.plane, a, par, v.es, g);
   deviations<L>(g, ref, drho, u[0], u[1], u[2]);
   float* d = du + (long long)run * L::D * v.plane + a.at(0, 0, 0);
 #pragma unroll
@@ -96,10 +96,10 @@ __global__ void __launch_bounds__(128)
   }
   if (x >= v.n[0] || y >= v.n[1]) return;
   if (inactive(v, x, y, z) || tn_node(v, x, y, z) || outer_layer<L>(v, x, y, z)) return;
-  S* f = static_cast<S*>(v.f) + run * v.run_stride;
+  S* f = run_ptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
-  load_pre<L, S>(f, v.plane, a, PAR, g);
+  load_pre<L, S>(f, v.plane, a, PAR, v.es, g);
   const float* d = du + (long long)run * L::D * v.plane;
   float up[3][3] = {}, um[3][3] = {};
 #pragma unroll
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128)
       g, omega, R,
       [&](auto I, float val) {
         constexpr int i = decltype(I)::value;
-        store_post_i<L, S, i>(f, v.plane, a, PAR, val);
+        store_post_i<L, S, i>(f, v.plane, a, PAR, v.es, val);
       },
       &hy);
 }
@@ -153,8 +153,8 @@ __global__ void k_parent_strain(LevelView p, LevelView c, RingDesc R, TnDesc T, 
     if (R.pper[a]) cc = ((cc % R.pn[a]) + R.pn[a]) % R.pn[a];
     P[a] = cc;
   }
-  const S* fp = static_cast<const S*>(p.f) + run * p.run_stride;
-  const S* fcb = static_cast<const S*>(c.f) + run * c.run_stride;
+  const S* fp = run_cptr<S>(p, run);
+  const S* fcb = run_cptr<S>(c, run);
   float up[3][3] = {}, um[3][3] = {};
   for (int ax = 0; ax < L::D; ++ax)
     for (int sg = 0; sg < 2; ++sg) {
@@ -166,11 +166,11 @@ __global__ void k_parent_strain(LevelView p, LevelView c, RingDesc R, TnDesc T, 
           Q[1] >= p.tn_lo[1] && Q[1] <= p.tn_hi[1] && Q[2] >= p.tn_lo[2] && Q[2] <= p.tn_hi[2]) {
         int X[3] = {0, 0, 0};
         for (int b = 0; b < L::D; ++b) X[b] = T.boxed[b] ? 2 * (Q[b] - T.lo[b]) : 2 * Q[b];
-        load_pre<L, S>(fcb, c.plane, node_addr<L>(c, X[0], X[1], X[2]), cpar, g);
+        load_pre<L, S>(fcb, c.plane, node_addr<L>(c, X[0], X[1], X[2]), cpar, c.es, g);
       } else if (mode == 0) {
-        load_pre<L, S>(fp, p.plane, node_addr<L>(p, Q[0], Q[1], Q[2]), ppar, g);
+        load_pre<L, S>(fp, p.plane, node_addr<L>(p, Q[0], Q[1], Q[2]), ppar, p.es, g);
       } else {
-        load_post<L, S>(fp, p.plane, node_addr<L>(p, Q[0], Q[1], Q[2]), ppar, g);
+        load_post<L, S>(fp, p.plane, node_addr<L>(p, Q[0], Q[1], Q[2]), ppar, p.es, g);
       }
       deviations<L>(g, ref, drho, u[0], u[1], u[2]);
       for (int b = 0; b < 3; ++b) (sg ? um : up)[ax][b] = u[b];
@@ -256,15 +256,15 @@ __global__ void k_collide_bnd(LevelView c, BndDesc B, RingDesc R, const float* s
   hy.ks = ks;
 #pragma unroll
   for (int j = 0; j < 6; ++j) hy.s[j] = 0.5f * Sv[j];  // eq. PijResc
-  S* fb = static_cast<S*>(c.f) + run * c.run_stride;
+  S* fb = run_ptr<S>(c, run);
   const NodeAddr a = node_addr<L>(c, X[0], X[1], X[2]);
   float g[L::Q];
-  load_pre<L, S>(fb, c.plane, a, par, g);
+  load_pre<L, S>(fb, c.plane, a, par, c.es, g);
   collide_emit<L, 3, MOV>(
       g, omega, ref,
       [&](auto I, float val) {
         constexpr int i = decltype(I)::value;
-        store_post_i<L, S, i>(fb, c.plane, a, par, val);
+        store_post_i<L, S, i>(fb, c.plane, a, par, c.es, val);
       },
       &hy);
 }

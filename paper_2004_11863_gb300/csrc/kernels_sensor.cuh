@@ -104,9 +104,9 @@ __global__ void k_sensors(LevelView v, const float* du, int par, SensorState st,
   const float e2 = st.eps * st.eps;
   const bool ac = pdiv * div < 0.0f && fabsf(pdiv) > st.eps && fabsf(div) > st.eps;
   const bool sh = pc[0] * cc[0] + pc[1] * cc[1] + pc[2] * cc[2] < 0.0f && np2 > e2 && nc2 > e2;
-  const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+  const S* f = run_cptr<S>(v, run);
   float g[L::Q];
-  load_pre<L, S>(f, v.plane, a, par, g);
+  load_pre<L, S>(f, v.plane, a, par, v.es, g);
   const float n2 = ghost_norm2<L>(g, ref);
   const bool gh = n2 > st.g2 && !ac && !sh;
   *fl = (unsigned char)((ac ? 1 : 0) | (sh ? 2 : 0) | (gh ? 4 : 0));

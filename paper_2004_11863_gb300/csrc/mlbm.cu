@@ -301,7 +301,9 @@ void build_view(lbm_ctx* h, int l) {
   const long long SZ = v.n[2] + 2 * g[2];
   w.off = 32 + ((long long)g[2] * w.SY + g[1]) * w.SX;
   long long need = w.off + SZ * w.SY * (long long)w.SX + 32;
-  w.plane = (need + 63) / 64 * 64;
+  // binary16 with two or more runs: runs interleaved in pairs (es = 2)
+  w.es = (h->cfg.storage == LBM_FP16_SHIFTED && h->batch >= 2) ? 2 : 1;
+  w.plane = (need + 63) / 64 * 64 * w.es;
   w.run_stride = w.plane * h->q;
   for (int a = 0; a < 3; ++a) {
     w.n[a] = v.n[a];
@@ -334,7 +336,7 @@ void build_view(lbm_ctx* h, int l) {
     }
     v.n_active = v.n_nodes - ina;
   }
-  v.bytes = (size_t)w.run_stride * h->batch *
+  v.bytes = (size_t)w.run_stride * ((h->batch + w.es - 1) / w.es) *
             (h->cfg.storage == LBM_FP16_SHIFTED ? 2 : 4);
 }
 

@@ -56,9 +56,38 @@ cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& 
   return cudaGetLastError();
 }
 
+template <class L, int COLL>
+cudaError_t sc_pair_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx,
+                           int by, cudaStream_t s) {
+  if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
+  dim3 block(bx, by, 1);
+  dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + by - 1) / by, v.n[2] * ((v.batch + 1) / 2));
+  const bool mov = ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
+  const RefF R = make_ref_f<L>(ref);
+  if (mov) {
+    if (par == 0)
+      k_stream_collide_pair<L, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+    else
+      k_stream_collide_pair<L, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+  } else {
+    if (par == 0)
+      k_stream_collide_pair<L, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+    else
+      k_stream_collide_pair<L, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+  }
+  return cudaGetLastError();
+}
+
 template <class L, class S>
 cudaError_t sc_coll(const LevelView& v, int coll, int par, float omega, const RefState& ref,
                     int bx, int by, cudaStream_t s) {
+  if (std::is_same<S, __half>::value && v.es == 2) {
+    switch (coll) {
+      case 0: return sc_pair_launch<L, 0>(v, par, omega, ref, bx, by, s);
+      case 1: return sc_pair_launch<L, 1>(v, par, omega, ref, bx, by, s);
+      default: return sc_pair_launch<L, 2>(v, par, omega, ref, bx, by, s);
+    }
+  }
   switch (coll) {
     case 0: return sc_launch<L, S, 0>(v, par, omega, ref, bx, by, s);
     case 1: return sc_launch<L, S, 1>(v, par, omega, ref, bx, by, s);
