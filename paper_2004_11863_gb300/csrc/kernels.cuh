@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
 template <class L>
 struct K1PairTune;
 #ifndef K1P_MINB_D2Q9
-#define K1P_MINB_D2Q9 8
+#define K1P_MINB_D2Q9 10
 #endif
 #ifndef K1P_MINB_D3Q19
 #define K1P_MINB_D3Q19 4
@@ -480,11 +480,20 @@ __global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new,
 // history value is read once per tile instead of once per stencil use, and
 // a node's serial work is split G ways (the kernel is latency-bound: a
 // surface's worth of nodes does not fill the GPU).
+#ifndef INJ_TJ_3D
+#define INJ_TJ_3D 8
+#endif
+#ifndef INJ_G_3D
+#define INJ_G_3D 1
+#endif
+#ifndef INJ_G_2D
+#define INJ_G_2D 4
+#endif
 template <class L>
 struct InjTile {
-  static constexpr int TI = 32;                   // along the first tangent axis
-  static constexpr int TJ = (L::D == 3) ? 4 : 1;  // along the second
-  static constexpr int G = (L::D == 3) ? 2 : 4;   // thread groups per node
+  static constexpr int TI = 32;                           // along the first tangent axis
+  static constexpr int TJ = (L::D == 3) ? INJ_TJ_3D : 1;  // along the second
+  static constexpr int G = (L::D == 3) ? INJ_G_3D : INJ_G_2D;  // thread groups per node
   static constexpr int WI = TI / 2 + 5;           // parent window (stencil reach)
   static constexpr int WJ = (L::D == 3) ? TJ / 2 + 5 : 1;
   static constexpr int NV = 4 + L::Q;
@@ -507,8 +516,9 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
     k_inject(LevelView c, InjDesc J, RingDesc R, float w0, float w1, float w2, int s_m1,
              int s_0, int s_p1, float resc, int par, RefF ref) {
   using T = InjTile<L>;
+  constexpr bool SPLIT = T::G > 1;  // a node's values shared through shared memory
   __shared__ float sv[T::NV][T::WJ][T::WI];
-  __shared__ float res[T::NV][T::TJ][T::TI];
+  __shared__ float res[SPLIT ? T::NV : 1][SPLIT ? T::TJ : 1][SPLIT ? T::TI : 1];
   const int run = blockIdx.y;
   // tile -> face, tile coordinates
   int f = 0;
@@ -572,29 +582,43 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
 #pragma unroll
   for (int b = 0; b < 3; ++b)
     if (b < a && J.boxed[b] && (Xn[b] == 0 || Xn[b] == c.n[b] - 1)) live = false;
-  if (live) {
-    // eq. spaceInt weights: -1/16 on the outer, 9/16 on the inner points
-    auto sw = [](int k) { return (k == 0 || k == 3) ? -1.0f / 16.0f : 9.0f / 16.0f; };
-    const bool oi = xi & 1, oj = (L::D == 3) && (xj & 1);
-    const int ni = oi ? 4 : 1, nj = oj ? 4 : 1;
-    // window index of the stencil's first point along each tangent axis
-    const int bi = (oi ? (xi - 3) / 2 : xi / 2) - p0i;
-    const int bj = (L::D == 3) ? ((oj ? (xj - 3) / 2 : xj / 2) - p0j) : 0;
-    for (int j = tz; j < T::NV; j += T::G) {
-      float acc = 0.0f;
-      for (int sj = 0; sj < nj; ++sj)
-        for (int si = 0; si < ni; ++si) {
-          const float w = (oi ? sw(si) : 1.0f) * (oj ? sw(sj) : 1.0f);
-          acc += w * sv[j][bj + sj][bi + si];
-        }
-      res[j][ty][tx] = acc;
-    }
+  // eq. spaceInt weights: -1/16 on the outer, 9/16 on the inner points
+  auto sw = [](int k) { return (k == 0 || k == 3) ? -1.0f / 16.0f : 9.0f / 16.0f; };
+  const bool oi = xi & 1, oj = (L::D == 3) && (xj & 1);
+  const int ni = oi ? 4 : 1, nj = oj ? 4 : 1;
+  // window index of the stencil's first point along each tangent axis
+  const int bi = (oi ? (xi - 3) / 2 : xi / 2) - p0i;
+  const int bj = (L::D == 3) ? ((oj ? (xj - 3) / 2 : xj / 2) - p0j) : 0;
+  auto interp = [&](int j) {
+    float acc = 0.0f;
+    for (int sj = 0; sj < nj; ++sj)
+      for (int si = 0; si < ni; ++si) {
+        const float w = (oi ? sw(si) : 1.0f) * (oj ? sw(sj) : 1.0f);
+        acc += w * sv[j][bj + sj][bi + si];
+      }
+    return acc;
+  };
+  // value j of this node: from the shared split (G > 1) or interpolated here
+  float own[SPLIT ? 1 : T::NV];
+  if constexpr (SPLIT) {
+    if (live)
+      for (int j = tz; j < T::NV; j += T::G) res[j][ty][tx] = interp(j);
+    __syncthreads();
+  } else {
+    if (live)
+#pragma unroll
+      for (int j = 0; j < T::NV; ++j) own[j] = interp(j);
   }
-  __syncthreads();
   if (!live) return;
+  auto val = [&](int j) {
+    if constexpr (SPLIT)
+      return res[j][ty][tx];
+    else
+      return own[j];
+  };
   // rebuild f = f0(rho, u) + resc f1 (eq. rescff), every G-th direction
-  const float drho = res[0][ty][tx], dux = res[1][ty][tx], duy = res[2][ty][tx];
-  const float duz = (L::D == 3) ? res[3][ty][tx] : 0.0f;
+  const float drho = val(0), dux = val(1), duy = val(2);
+  const float duz = (L::D == 3) ? val(3) : 0.0f;
   const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;
   const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
   float A[7], dA[7];
@@ -607,7 +631,7 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
     constexpr int i = decltype(I)::value;
     if (i % T::G == tz) {
       const float g = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
-                      resc * res[4 + i][ty][tx];
+                      resc * val(4 + i);
       store_pre_i<L, S, i>(fb, c.plane, ad, par, c.es, g);
     }
   });
