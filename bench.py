@@ -43,10 +43,11 @@ FALLBACK_HBM_GBS = 6800.0
 # sources it was taken on; ignored once the sources change.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the fine-level
-    # update of the 33-run benchmark (parity 1: 331.6 + 262.3 MB; parity 0:
-    # 331.6 + 255.1 MB); stored per run so that any batch scales it.
-    ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 590.2e6 / 33,
-                                       "src": "f29bec115bee9fa6"},
+    # update of the 33-run benchmark (mean of two odd launches, 593.6 and
+    # 590.7 MB, and two even ones, 586.5 and 586.7 MB); stored per run so that
+    # any batch scales it.
+    ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 589.4e6 / 33,
+                                       "src": "a07748673a116ad7"},
 }
 
 
@@ -232,7 +233,6 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=48, help="requests of the serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -404,25 +404,51 @@ def main():
         gv.close()
 
     # ---------------- serving: continuous batching vs one run at a time -----
+    # Capacities (every request there at the start) of plain one-run-at-a-
+    # time stepping in FP32 and FP16 and of the FP16 server; then the server
+    # under Poisson arrivals at 0.5x and 2x the sequential FP32 capacity
+    # (the same seeded runs, arrival times rescaled).
     serving = None
     if args.serve > 0:
         from paper_2004_11863_gb300 import serve as SV
-        reqs = W.serving_requests(args.serve, rate=args.serve_rate, step_scale=0.1,
-                                  size_scale=0.5)
-        served = SV.Server(hbm_budget=32e9, max_active=32, streams=16, chunk=25,
-                           storage="fp16").run(reqs)
-        seq = SV.serve_sequential(reqs, storage="fp32")
+        mk = lambda rate: W.serving_requests(args.serve, rate=rate, step_scale=0.1,
+                                             size_scale=0.5)
+        new_server = lambda: SV.Server(hbm_budget=32e9, max_active=32, streams=16, chunk=25,
+                                       storage="fp16")
+        base = mk(1.0)
+        SV.serve_sequential(base[:4], storage="fp16", realtime=False)  # warm-up
+
+        def fig(r):
+            return {"runs_per_s": round(r["runs_per_s"], 2), "p50_s": round(r["p50_s"], 4),
+                    "p99_s": round(r["p99_s"], 4), "unstable": r["unstable"]}
+
+        seq32 = SV.serve_sequential(base, storage="fp32", realtime=False)
+        seq16 = SV.serve_sequential(base, storage="fp16", realtime=False)
+        cap = new_server().run(base, realtime=False)
+        C = seq32["runs_per_s"]
+        loads = {}
+        for f in (0.5, 2.0):
+            r = new_server().run(mk(f * C), realtime=True)
+            loads[f"{f}x"] = {**fig(r), "arrival_rate_per_s": round(f * C, 1),
+                              "max_concurrent": r["max_concurrent"]}
+        # accuracy: the served FP16 results are those of sequential FP16
+        # stepping bit for bit; their deviation from FP32 at the probes
+        same16 = all(np.array_equal(a.probes, b.probes) and np.array_equal(a.mass, b.mass)
+                     for a, b in zip(cap["results"], seq16["results"]))
+        d16 = max(float(np.max(np.abs(a.probes - b.probes)))
+                  for a, b in zip(cap["results"], seq32["results"]))
         serving = {
-            "requests": args.serve, "arrival_rate_per_s": args.serve_rate,
+            "requests": args.serve,
             "stream": "seeded mix of D2Q9/D3Q19/D3Q27, 1-3 levels, Ma 0.05-0.2, "
                       "tau-1/2 in [1e-5,1e-2], vortex/pulse; sides x0.5, steps x0.1",
-            "served_fp16": {"runs_per_s": round(served["runs_per_s"], 2),
-                            "p50_s": round(served["p50_s"], 4), "p99_s": round(served["p99_s"], 4),
-                            "unstable": served["unstable"],
-                            "max_concurrent": served["max_concurrent"]},
-            "sequential_fp32": {"runs_per_s": round(seq["runs_per_s"], 2),
-                                "p50_s": round(seq["p50_s"], 4), "p99_s": round(seq["p99_s"], 4),
-                                "unstable": seq["unstable"]},
+            "capacity": {"sequential_fp32": fig(seq32), "sequential_fp16": fig(seq16),
+                         "served_fp16": {**fig(cap), "max_concurrent": cap["max_concurrent"]}},
+            "served_fp16_under_load": loads,
+            "accuracy": {"served_fp16_equals_sequential_fp16_bitwise": bool(same16),
+                         "max_abs_probe_diff_fp16_vs_fp32": d16},
+            "note": "server: continuous batching, up to 32 resident runs on 16 streams, "
+                    "device memory from the caching allocator; sequential: one run at a time "
+                    "with the library's defaults",
         }
 
     if rank != 0:

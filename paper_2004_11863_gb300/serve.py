@@ -66,7 +66,14 @@ def probe_nodes(case: workloads.Case) -> np.ndarray:
 
 class Server:
     def __init__(self, hbm_budget: float = 32e9, max_active: int = 64, streams: int = 16,
-                 chunk: int = 25, storage: str = "fp16", moving_reference: bool = True):
+                 chunk: int = 25, storage: str = "fp16", moving_reference: bool = True,
+                 torch_allocator: bool = True, graph_min_steps: int = 0):
+        """torch_allocator: take each run's device memory from PyTorch's
+        caching allocator (no cudaMalloc / cudaFree, and their
+        synchronisation, per run).  graph_min_steps: runs with fewer coarse
+        steps than this launch their kernels directly instead of capturing a
+        CUDA graph per step phase (capture costs more than it saves on short
+        runs)."""
         import torch
         self.torch = torch
         self.budget = float(hbm_budget)
@@ -74,6 +81,8 @@ class Server:
         self.chunk = chunk
         self.storage = storage
         self.moving_reference = moving_reference
+        self.torch_allocator = torch_allocator
+        self.graph_min_steps = graph_min_steps
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self._next_stream = 0
 
@@ -87,7 +96,10 @@ class Server:
         self._next_stream += 1
         u_ref = case.u_ref if self.moving_reference else (0.0, 0.0, 0.0)
         h = mlbm.Lbm(case.lattice, case.collision, case.tau0, case.dims, case.boxes,
-                     storage=self.storage, stream=stream.cuda_stream, u_ref=u_ref)
+                     storage=self.storage, stream=stream.cuda_stream, u_ref=u_ref,
+                     torch_allocator=self.torch_allocator)
+        if case.steps < self.graph_min_steps:
+            h.set_graphs(False)
         h.init_analytic(case.ic)
         h.probe_add(case.nlevels - 1, probe_nodes(case))
         return h, stream
@@ -133,7 +145,8 @@ class Server:
                 if a.done_steps >= a.req.case.steps:
                     rec = a.h.probe(max_steps=1)
                     mass, _, stable = a.h.diag()
-                    results.append(Result(a.req.rid, a.req.arrival, a.admitted,
+                    arrival = a.req.arrival if realtime else 0.0
+                    results.append(Result(a.req.rid, arrival, a.admitted,
                                           time.perf_counter() - t0, rec[-1, 0], mass, stable))
                     a.h.close()
                     used -= a.bytes
@@ -162,10 +175,11 @@ class Server:
 
 
 def serve_sequential(requests: List[workloads.Request], storage: str = "fp32",
-                     moving_reference: bool = True) -> Dict:
+                     moving_reference: bool = True, realtime: bool = True) -> Dict:
     """Plain one-run-at-a-time stepping (the comparison for the server):
-    each request waits for the previous one, runs alone, then its result is
-    read back."""
+    each request waits for the previous one, runs alone with the library's
+    defaults, then its result is read back.  realtime=False: every request
+    is there at the start (the measured figure is then a capacity)."""
     s = Server(max_active=1, streams=1, chunk=1 << 30, storage=storage,
-               moving_reference=moving_reference)
-    return s.run(requests, realtime=True)
+               moving_reference=moving_reference, torch_allocator=False)
+    return s.run(requests, realtime=realtime)

@@ -1,5 +1,6 @@
-"""Continuous-batching server: results are identical alone and in the mix,
-the memory budget holds, and a served run matches the FP64 oracle."""
+"""Continuous-batching server: results are identical alone and in the mix
+(and with either device allocator), the memory budget holds, and a served
+run matches the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -29,7 +30,10 @@ def test_results_same_alone_and_in_the_mix(S):
     mixed = S.Server(hbm_budget=8e9, max_active=8, streams=4, chunk=7).run(reqs)
     assert mixed["max_concurrent"] > 1
     for r in reqs:
-        alone = S.Server(max_active=1, streams=1, chunk=7).run([W.Request(r.rid, 0.0, r.case)])
+        # alone, and with device memory from cudaMalloc instead of the
+        # caching allocator: the same bits
+        alone = S.Server(max_active=1, streams=1, chunk=7, torch_allocator=False).run(
+            [W.Request(r.rid, 0.0, r.case)])
         a = alone["results"][0]
         m = [x for x in mixed["results"] if x.rid == r.rid][0]
         assert np.array_equal(a.probes, m.probes), r.rid
