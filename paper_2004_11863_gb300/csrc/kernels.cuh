@@ -27,6 +27,7 @@
 
 #include "desc.h"
 #include "lattice.cuh"
+#include "lattice_x2.cuh"
 
 namespace mlbm {
 
@@ -328,8 +329,9 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
 
 // Level update of binary16 storage with runs interleaved in pairs (es = 2):
 // one thread updates one node of runs 2p and 2p+1, moving each direction of
-// both runs with one 4-byte access (a half2 of the two runs' values); the
-// two collisions are the same arithmetic as k_stream_collide's.  The last
+// both runs with one 4-byte access (a half2 of the two runs' values), and
+// computes the two collisions as one two-lane collision on the packed FP32
+// instructions (lattice_x2.cuh).  The last
 // pair of an odd batch carries an unused run that stays at rest (zero
 // deviations collide to zero; no interface kernel touches it).
 template <class L>
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
   __half2* f = reinterpret_cast<__half2*>(static_cast<__half*>(v.f) + pair * v.run_stride);
   const long long ph = v.plane / 2;
   const NodeAddr a = node_addr<L>(v, x, y, z);
-  float ga[L::Q], gb[L::Q];
+  F2 g[L::Q];  // lane x: run 2p, lane y: run 2p+1
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     __half2 h;
@@ -380,18 +382,11 @@ __global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
       h = f[i * ph + a.at(0, 0, 0)];
     else
       h = f[opp<L>(i) * ph + a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))];
-    const float2 t = __half22float2(h);
-    ga[i] = t.x;
-    gb[i] = t.y;
+    g[i].v = __half22float2(h);
   });
-  float pa[L::Q];
-  collide_emit<L, COLL, MOV>(ga, omega, R, [&](auto I, float val) {
+  collide_emit_x2<L, COLL, MOV>(g, omega, R, [&](auto I, F2 val) {
     constexpr int i = decltype(I)::value;
-    pa[i] = val;
-  });
-  collide_emit<L, COLL, MOV>(gb, omega, R, [&](auto I, float val) {
-    constexpr int i = decltype(I)::value;
-    const __half2 h = __floats2half2_rn(pa[i], val);
+    const __half2 h = __float22half2_rn(val.v);
     if constexpr (PAR == 0)
       f[opp<L>(i) * ph + a.at(0, 0, 0)] = h;
     else

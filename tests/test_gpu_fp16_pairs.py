@@ -1,11 +1,21 @@
 """Binary16 storage with the runs of a batch interleaved in pairs (one 4-byte
-access moves a node's population of two runs): every run of a batch must
-equal the same run stepped alone (single-run layout, one run per launch), on
-every kernel of the step — level updates, interface transfers, read-outs —
-for odd and even batches, rest and moving reference states, and H-RR."""
+access moves a node's population of two runs, and the two collisions run
+as one two-lane collision on the packed FP32 instructions).
+
+Each lane computes exactly the same instructions on its own run, so a run's
+result does not depend on its partner or on which lane holds it: checked bit
+for bit by permuting a batch's runs.  The two-lane collision fuses products
+and sums where the single-run collision may round them separately, so a
+paired run and the same run stepped alone may differ in the last bit of a
+binary32 intermediate, which a binary16 rounding can turn into one binary16
+ulp: each paired run is checked against the FP64 oracle within the
+stated binary16 bound, and against the single run within twice it.  All kernels of the step are
+exercised (level updates, interface transfers, read-outs), for odd and even
+batches, rest and moving reference states, and H-RR."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2004_11863_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -37,22 +47,67 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("batch", [2, 3])
-@pytest.mark.parametrize("key", list(CASES))
-def test_paired_batch_equals_single_runs(M, key, batch):
-    case = CASES[key]()
-    ics = [case, _other(case), case][:batch]
-    g = M.Lbm.from_case(case, storage="fp16", batch=batch, init=False)
+def _bound(c, u_ref, steps):
+    """The stated binary16 bound (see test_gpu_parity.fp16_bound) with the
+    stored magnitude measured against the reference state the run is stored
+    against, g = f - f0(rho0, U): a run at rest stored against a moving
+    reference keeps deviations of order w 3 xi.U, not of order its own
+    perturbation."""
+    o = oracle.Run.from_case(c)
+    f0 = oracle.feq(c.lattice, c.rho0, u_ref)
+    gmax = max(float(np.max(np.abs(o.populations(l) - f0[:, None]))) for l in range(c.nlevels))
+    n = steps * 2 ** (c.nlevels - 1)
+    return 2.0 * np.sqrt(c.q) * 2.0 ** -11 * gmax * np.sqrt(n), o
+
+
+def _init(M, case, ics):
+    g = M.Lbm.from_case(case, storage="fp16", batch=len(ics), init=False)
     for b, c in enumerate(ics):
         for l in range(case.nlevels):
             g.init(l, b, *W.initial_fields(c, l))
+    return g
+
+
+@pytest.mark.parametrize("key", list(CASES))
+def test_run_independent_of_lane_and_partner(M, key):
+    case = CASES[key]()
+    A, B = case, _other(case)
+    g1 = _init(M, case, [A, B, A])  # A in lane x beside B, A in lane x beside the spare
+    g2 = _init(M, case, [B, A])     # A in lane y
+    g1.step(5)
+    g2.step(5)
+    for l in range(case.nlevels):
+        ref = g1.macros(l, 0)
+        for other in (g1.macros(l, 2), g2.macros(l, 1)):
+            assert np.array_equal(ref[0], other[0], equal_nan=True)
+            assert np.array_equal(ref[1], other[1], equal_nan=True)
+        rb1, ub1 = g1.macros(l, 1)
+        rb2, ub2 = g2.macros(l, 0)
+        assert np.array_equal(rb1, rb2, equal_nan=True) and np.array_equal(ub1, ub2, equal_nan=True)
+
+
+@pytest.mark.parametrize("batch", [2, 3])
+@pytest.mark.parametrize("key", list(CASES))
+def test_paired_batch_matches_single_runs(M, key, batch):
+    case = CASES[key]()
+    ics = [case, _other(case), case][:batch]
+    g = _init(M, case, ics)
     g.step(5)
     for b, c in enumerate(ics):
         s = M.Lbm.from_case(c, storage="fp16", u_ref=case.u_ref)
         s.step(5)
+        tol, o = _bound(c, case.u_ref, 5)
+        o.step(5)
         for l in range(case.nlevels):
             ra, ua = g.macros(l, b)
             rb, ub = s.macros(l)
-            assert np.array_equal(ra, rb, equal_nan=True), (b, l, np.nanmax(np.abs(ra - rb)))
-            assert np.array_equal(ua, ub, equal_nan=True), (b, l, np.nanmax(np.abs(ua - ub)))
+            ro, uo = o.macros(l)
+            m = ~np.isnan(ro)
+            assert np.array_equal(np.isnan(ra), ~m) and np.array_equal(np.isnan(rb), ~m)
+            # the paired run within the bound of the exact result, and hence
+            # within twice the bound of the same run stepped alone
+            assert np.max(np.abs(ra[m] - ro[m])) <= tol, (b, l)
+            assert np.max(np.abs(ua[:, m] - uo[:, m])) <= tol, (b, l)
+            assert np.max(np.abs(ra[m] - rb[m])) <= 2 * tol, (b, l)
+            assert np.max(np.abs(ua[:, m] - ub[:, m])) <= 2 * tol, (b, l)
         s.close()
