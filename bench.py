@@ -47,14 +47,14 @@ NCU_TRAFFIC = {
     # 590.7 MB, and two even ones, 586.5 and 586.7 MB); stored per run so that
     # any batch scales it.
     ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 589.4e6 / 33,
-                                       "src": "a07748673a116ad7"},
+                                       "src": "953a1153897e51a6"},
 }
 
 
 def kernel_source_hash() -> str:
     """Hash of the level update's source: lattice.cuh (the collision) and the
-    level-update section of kernels.cuh (addressing helpers, launch shapes,
-    k_stream_collide).  Edits elsewhere do not void a traffic capture."""
+    section of kernels.cuh from the addressing helpers through
+    k_stream_collide.  Edits elsewhere do not void a traffic capture."""
     csrc = os.path.join(ROOT, "paper_2004_11863_gb300", "csrc")
     h = hashlib.sha256()
     with open(os.path.join(csrc, "lattice.cuh"), "rb") as fh:
@@ -62,7 +62,7 @@ def kernel_source_hash() -> str:
     with open(os.path.join(csrc, "kernels.cuh"), "r") as fh:
         k = fh.read()
     start = k.index("__device__ __forceinline__ int wrapi")
-    end = k.index("// (drho, du, f^(1)) of a population set")
+    end = k.index("// Level update of binary16 storage with runs interleaved in pairs")
     h.update(k[start:end].encode())
     return h.hexdigest()[:16]
 
