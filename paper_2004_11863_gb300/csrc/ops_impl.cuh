@@ -33,9 +33,33 @@ RefF make_ref_f(const RefState& r) {
   return R;
 }
 
+template <class L, int COLL>
+cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx,
+                         int by, cudaStream_t s) {
+  if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
+  dim3 block(bx, by, 1);
+  dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + 2 * by - 1) / (2 * by), v.n[2] * v.batch);
+  const bool mov = ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
+  const RefF R = make_ref_f<L>(ref);
+  if (mov) {
+    if (par == 0)
+      k_stream_collide_x2<L, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+    else
+      k_stream_collide_x2<L, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+  } else {
+    if (par == 0)
+      k_stream_collide_x2<L, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+    else
+      k_stream_collide_x2<L, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+  }
+  return cudaGetLastError();
+}
+
 template <class L, class S, int COLL>
 cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx, int by,
                       cudaStream_t s) {
+  if constexpr (std::is_same<S, float>::value && K1X2Tune<L>::ON)
+    return sc_x2_launch<L, COLL>(v, par, omega, ref, bx, by, s);
   constexpr int NPT = K1Tune<L, S>::NPT;
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);
