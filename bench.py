@@ -47,13 +47,13 @@ NCU_TRAFFIC = {
     # 590.7 MB, and two even ones, 586.5 and 586.7 MB); stored per run so that
     # any batch scales it.
     ("pulse2d", "fp32", "update_L1"): {"bytes_per_launch_per_run": 589.4e6 / 33,
-                                       "src": "953a1153897e51a6"},
+                                       "src": "4fb2ccd7fdd98bb4"},
 }
 
 
 def kernel_source_hash() -> str:
     """Hash of the level update's source: lattice.cuh (the collision) and the
-    section of kernels.cuh from the addressing helpers through
+    part of kernels.cuh from the addressing helpers to the end of
     k_stream_collide.  Edits elsewhere do not void a traffic capture."""
     csrc = os.path.join(ROOT, "paper_2004_11863_gb300", "csrc")
     h = hashlib.sha256()
@@ -62,7 +62,8 @@ def kernel_source_hash() -> str:
     with open(os.path.join(csrc, "kernels.cuh"), "r") as fh:
         k = fh.read()
     start = k.index("__device__ __forceinline__ int wrapi")
-    end = k.index("// Level update of binary16 storage with runs interleaved in pairs")
+    end = k.index("k_stream_collide(LevelView v, float omega, RefF R)")
+    end = k.index("\n}\n", end) + 3  # the end of k_stream_collide
     h.update(k[start:end].encode())
     return h.hexdigest()[:16]
 
@@ -99,7 +100,7 @@ class ClockSampler:
                     self.samples.append([x.strip() for x in out.split(",")])
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.05)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -225,7 +226,7 @@ KERNEL_KINDS = ((0, "update"), (1, "capture"), (2, "inject"), (3, "restrict"), (
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="pulse2d")
