@@ -135,6 +135,15 @@ struct InjDesc {
   int boxed[3];
 };
 
+// Tiles of TN nodes for the face-tiled restriction: face f's TN nodes form
+// a rectangle along its tangent axes t1, t2; a tile covers up to TI x TJ of
+// them (tiles of face f are numbered from tstart[f], t1 fastest).
+struct RstDesc {
+  int t1[kMaxFaces], t2[kMaxFaces];
+  int ntile1[kMaxFaces];
+  long long tstart[kMaxFaces + 1];
+};
+
 // Parent-level f->c nodes (TN, the parent nodes one parent cell inside the
 // child box), one entry per node.  Face f covers box-relative coordinates
 // rlo[f][a] .. rlo[f][a] + rext[f][a] - 1 along each axis (absolute parent

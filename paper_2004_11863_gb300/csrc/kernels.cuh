@@ -7,10 +7,15 @@
 //   k_inject          child TF / IE nodes: temporal (eq. TempInt) and spatial
 //                     (eq. spaceInt) interpolation staged per face tile in
 //                     shared memory, rescaling (eq. rescff), written where
-//                     the child's next update reads them;
-//   k_restrict        parent TN nodes: filtered child f^(1) (eq. filterFneq),
+//                     the child's next update reads them (2D; k_inject_sep,
+//                     the same with the stencil applied one axis at a time,
+//                     in 3D);
+//   k_restrict_tile   parent TN nodes: filtered child f^(1) (eq. filterFneq),
 //                     rescaling (eq. rescfc), written where the parent's next
-//                     update reads them (the restriction);
+//                     update reads them (the restriction), per face tile
+//                     (k_restrict: one thread per TN node and filter
+//                     neighbour, kept for the hybrid collision, which also
+//                     collides the TN nodes);
 //   k_init / k_macros / k_diag_* / k_probe   set-up and read-out.
 //
 // AA pattern.  A step of parity 0 reads g_i of node n from plane i at n and
@@ -591,6 +596,34 @@ __device__ __forceinline__ void store_pre_i(S* f, long long plane, const NodeAdd
         f + (long long)opp<L>(I) * plane + es * a.at(-L::c(I, 0), -L::c(I, 1), -L::c(I, 2)), v);
 }
 
+// Rebuild f = f0(rho, u) + resc f^(1) (eq. rescff) of child node (x, y, z)
+// from its interpolated values val(j) = (drho, du, f^(1)) and store, from
+// thread group grp of G, every G-th direction where the child's update of
+// parity par reads it.
+template <class L, class S, int G, class V>
+__device__ __forceinline__ void inject_rebuild(const LevelView& c, int run, int x, int y, int z,
+                                               int par, float resc, const RefF& ref, int grp,
+                                               V val) {
+  const float drho = val(0), dux = val(1), duy = val(2);
+  const float duz = (L::D == 3) ? val(3) : 0.0f;
+  const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;
+  const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
+  float A[7], dA[7];
+  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, A, dA);
+  const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
+  const float rho = ref.rho0 + drho;
+  S* fb = run_ptr<S>(c, run);
+  const NodeAddr ad = node_addr<L>(c, x, y, z);
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (i % G == grp) {
+      const float g = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
+                      resc * val(4 + i);
+      store_pre_i<L, S, i>(fb, c.plane, ad, par, c.es, g);
+    }
+  });
+}
+
 template <class L, class S>
 __global__ void __launch_bounds__(InjTile<L>::NT)
     k_inject(LevelView c, InjDesc J, RingDesc R, float w0, float w1, float w2, int s_m1,
@@ -696,25 +729,119 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
     else
       return own[j];
   };
-  // rebuild f = f0(rho, u) + resc f1 (eq. rescff), every G-th direction
-  const float drho = val(0), dux = val(1), duy = val(2);
-  const float duz = (L::D == 3) ? val(3) : 0.0f;
-  const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;
-  const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
-  float A[7], dA[7];
-  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, A, dA);
-  const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
-  const float rho = ref.rho0 + drho;
-  S* fb = run_ptr<S>(c, run);
-  const NodeAddr ad = node_addr<L>(c, Xn[0], Xn[1], Xn[2]);
-  sfor<L::Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    if (i % T::G == tz) {
-      const float g = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
-                      resc * val(4 + i);
-      store_pre_i<L, S, i>(fb, c.plane, ad, par, c.es, g);
+  inject_rebuild<L, S, T::G>(c, run, Xn[0], Xn[1], Xn[2], par, resc, ref, tz, val);
+}
+
+// 3D rebuild with the tensor-product stencil of eq. spaceInt applied one
+// axis at a time: the block stages the temporally interpolated parent window
+// (TI / 2 + 3 by TJ / 2 + 3 parent nodes: exactly what the tile's stencils
+// reach), interpolates it along t1 for every window row into shared memory
+// (every thread the same four taps, even child positions weighting their
+// co-located parent node by one), then each node interpolates along t2 (a
+// warp holds one child row, so one or four taps uniformly) and rebuilds.
+template <class L>
+struct InjSep {
+  static constexpr int TI = InjTile<L>::TI, TJ = InjTile<L>::TJ;
+  static constexpr int WI = TI / 2 + 3, WJ = TJ / 2 + 3;
+  static constexpr int NV = 4 + L::Q;
+  static constexpr int NT = TI * TJ;
+};
+
+template <class L, class S>
+__global__ void __launch_bounds__(InjSep<L>::NT)
+    k_inject_sep(LevelView c, const __grid_constant__ InjDesc J,
+                 const __grid_constant__ RingDesc R, float w0, float w1, float w2, int s_m1,
+                 int s_0, int s_p1, float resc, int par, RefF ref) {
+  static_assert(L::D == 3, "k_inject_sep is the 3D rebuild");
+  using T = InjSep<L>;
+  __shared__ float sv[T::NV][T::WJ][T::WI];  // parent window, interpolated in time
+  __shared__ float ta[T::NV][T::WJ][T::TI];  // ... and along t1
+  const int run = blockIdx.y;
+  int f = 0;
+  while (f + 1 < J.nf && (long long)blockIdx.x >= J.tstart[f + 1]) ++f;
+  const int tile = (int)(blockIdx.x - J.tstart[f]);
+  const int a = J.axis[f], t1 = J.t1[f], t2 = J.t2[f];
+  const int X0 = (tile % J.ntile1[f]) * T::TI;
+  const int Y0 = (tile / J.ntile1[f]) * T::TJ;
+  const int p0i = (X0 >> 1) - 1, p0j = (Y0 >> 1) - 1;  // window origin (parent)
+  auto pick = [](const int (&v)[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); };
+  const long long ext0 = R.ext[f][0], ext01 = ext0 * R.ext[f][1];
+  const long long st1 = t1 == 0 ? 1 : (t1 == 1 ? ext0 : ext01);
+  const long long st2 = t2 == 0 ? 1 : (t2 == 1 ? ext0 : ext01);
+  const int bx1 = pick(R.boxed, t1), bx2 = pick(R.boxed, t2);
+  const int e1 = pick(R.ext[f], t1), e2 = pick(R.ext[f], t2);
+  const int pn1 = pick(R.pn, t1), pn2 = pick(R.pn, t2);
+  const float* h = R.hist + (long long)run * 3 * R.nv * R.K;
+  const long long K = R.K, nv = R.nv;
+  const int tid = threadIdx.y * T::TI + threadIdx.x;
+  // stage (eq. TempInt)
+#pragma unroll 4
+  for (int e = tid; e < T::NV * T::WJ * T::WI; e += T::NT) {
+    const int pi = e % T::WI, pj = (e / T::WI) % T::WJ, vv = e / (T::WI * T::WJ);
+    int ri = p0i + pi, rj = p0j + pj;
+    bool ok = true;
+    long long idx = R.start[f];
+    if (bx1) {
+      ok = ok && ri >= -1 && ri <= e1 - 2;
+      idx += (long long)(ri + 1) * st1;
+    } else {
+      ri = ((ri % pn1) + pn1) % pn1;
+      idx += (long long)ri * st1;
     }
-  });
+    if (bx2) {
+      ok = ok && rj >= -1 && rj <= e2 - 2;
+      idx += (long long)(rj + 1) * st2;
+    } else {
+      rj = ((rj % pn2) + pn2) % pn2;
+      idx += (long long)rj * st2;
+    }
+    float val = 0.0f;
+    if (ok)
+      val = w0 * h[((long long)s_m1 * nv + vv) * K + idx] +
+            w1 * h[((long long)s_0 * nv + vv) * K + idx] +
+            w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+    sv[vv][pj][pi] = val;
+  }
+  __syncthreads();
+  // along t1 (eq. spaceInt weights -1/16, 9/16, 9/16, -1/16 at odd child
+  // positions; weight 1 on the co-located parent node at even ones)
+  {
+    const int tx = threadIdx.x;  // the child position along t1 is X0 + tx
+    const bool odd = tx & 1;
+    const int b = odd ? (tx - 1) >> 1 : tx >> 1;  // first tap in the window
+    const float wa = odd ? -1.0f / 16.0f : 0.0f, wb = odd ? 9.0f / 16.0f : 1.0f;
+    const float wc = odd ? 9.0f / 16.0f : 0.0f, wd = odd ? -1.0f / 16.0f : 0.0f;
+    for (int r = threadIdx.y; r < T::NV * T::WJ; r += T::TJ) {
+      const float* row = &sv[0][0][0] + r * T::WI + b;
+      ta[0][0][r * T::TI + tx] = wa * row[0] + wb * row[1] + wc * row[2] + wd * row[3];
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int xi = X0 + tx, xj = Y0 + ty;
+  const int xa = J.side[f] ? pick(c.n, a) - 1 : 0;
+  auto co = [&](int k) { return k == a ? xa : (k == t1 ? xi : xj); };
+  const int Xn0 = co(0), Xn1 = co(1), Xn2 = co(2);
+  bool live = xi < pick(c.n, t1) && xj < pick(c.n, t2);
+  // each boundary node is written by the first face (lowest axis) holding it
+  if (a > 0 && J.boxed[0] && (Xn0 == 0 || Xn0 == c.n[0] - 1)) live = false;
+  if (a > 1 && J.boxed[1] && (Xn1 == 0 || Xn1 == c.n[1] - 1)) live = false;
+  if (!live) return;
+  // along t2: one tap (even xj) or four (odd xj), uniform over the warp
+  float own[T::NV];
+  if (ty & 1) {
+    const int b = (ty - 1) >> 1;
+#pragma unroll
+    for (int j = 0; j < T::NV; ++j)
+      own[j] = -1.0f / 16.0f * ta[j][b][tx] + 9.0f / 16.0f * ta[j][b + 1][tx] +
+               9.0f / 16.0f * ta[j][b + 2][tx] - 1.0f / 16.0f * ta[j][b + 3][tx];
+  } else {
+    const int b = (ty >> 1) + 1;
+#pragma unroll
+    for (int j = 0; j < T::NV; ++j) own[j] = ta[j][b][tx];
+  }
+  inject_rebuild<L, S, 1>(c, run, Xn0, Xn1, Xn2, par, resc, ref, 0,
+                          [&](int j) { return own[j]; });
 }
 
 // Strain rate S = (grad u + grad u^T) / 2 by second-order central
@@ -864,6 +991,161 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
       store_pre<L, S>(fp, p.plane, a, ppar, es, g);
     }
   }
+}
+
+// Face-tiled restriction (plain and regularized collisions).  The filter of
+// eq. filterFneq is a tensor product of (1/4, 1/2, 1/4) along each axis, so
+// a block that owns TI x TJ TN nodes of one face first forms, for every
+// child node column of the tile's footprint (2 TI + 1 by 2 TJ + 1 columns
+// along the face's tangent axes t1, t2), the normal-axis sum of the three
+// children's weighted f^(1) -- each child node's f^(1) once per tile instead
+// of once per TN node that uses it -- keeps them in shared memory, filters
+// along t1 and t2 there, and rebuilds and stores the TN nodes with G threads
+// per node (each for every G-th direction), t1-consecutive nodes on
+// consecutive threads.  In the first step three consecutive lanes take the
+// three children of one column (ten columns per warp), so that on faces
+// normal to x one warp load fetches three neighbouring values per row
+// instead of one, and the column's sum is formed by two warp shuffles in a
+// fixed order.
+#ifndef RST_TJ_3D
+#define RST_TJ_3D 4
+#endif
+#ifndef RST_MINB_3D
+#define RST_MINB_3D 3
+#endif
+template <class L>
+struct RstTile {
+  static constexpr int TI = (L::D == 3) ? 14 : 29;      // TN nodes along t1
+  static constexpr int TJ = (L::D == 3) ? RST_TJ_3D : 1;  // ... along t2
+  static constexpr int FI = 2 * TI + 1;                 // footprint columns along t1
+  static constexpr int FJ = (L::D == 3) ? 2 * TJ + 1 : 1;
+  static constexpr int NCH = (FI + 9) / 10;             // ten-column chunks per footprint row
+  static constexpr int NW = (L::D == 3) ? FJ : 3;       // warps
+  static constexpr int NT = 32 * NW;
+  static constexpr int NN = TI * TJ;                    // TN nodes per tile
+  static constexpr int G = NT / NN;                     // threads per TN node in the rebuild
+  static constexpr int MINB = (L::D == 3) ? RST_MINB_3D : 8;  // resident blocks per SM
+};
+
+template <class L, class S>
+__global__ void __launch_bounds__(RstTile<L>::NT, RstTile<L>::MINB)
+    k_restrict_tile(LevelView p, LevelView c, const __grid_constant__ TnDesc T,
+                    const __grid_constant__ RstDesc J, float resc, int ppar, int cpar,
+                    RefF ref) {
+  using TT = RstTile<L>;
+  constexpr int Q = L::Q, TI = TT::TI, TJ = TT::TJ, FI = TT::FI, FJ = TT::FJ;
+  __shared__ float A[Q][FJ][FI];    // normal-filtered f^(1) per footprint column
+  __shared__ float Cf[Q][TJ][TI];   // fully filtered f^(1) per TN node
+  __shared__ float cm[TJ][TI][4];   // (drho, du) of the co-located child node
+  const int run = blockIdx.y;
+  int f = 0;
+  while (f + 1 < T.nf && (long long)blockIdx.x >= J.tstart[f + 1]) ++f;
+  const int tile = (int)(blockIdx.x - J.tstart[f]);
+  const int a = T.axis[f], t1 = J.t1[f], t2 = J.t2[f];
+  // per-face values picked by axis without indexing local arrays
+  auto pick = [](const int (&v)[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); };
+  const int ti = tile % J.ntile1[f], tj = tile / J.ntile1[f];
+  const int r1 = pick(T.rlo[f], t1) + ti * TI;  // first TN coordinate of the tile along t1, t2
+  const int r2 = pick(T.rlo[f], t2) + tj * TJ;
+  const int n1 = min(TI, pick(T.rlo[f], t1) + pick(T.rext[f], t1) - r1);
+  const int n2 = min(TJ, pick(T.rlo[f], t2) + pick(T.rext[f], t2) - r2);
+  const int ra = pick(T.rlo[f], a);
+  // 1. normal-axis sums of the footprint columns
+  {
+    const int lane = threadIdx.x, col = lane / 3, d = lane - 3 * col - 1;
+    const float w = d == 0 ? 0.5f : 0.25f;
+    int xa = 2 * ra + d;
+    if (pick(c.per, a)) xa = wrapi(xa, pick(c.n, a));
+    const S* fcb = run_cptr<S>(c, run);
+    for (int ch = threadIdx.y; ch < FJ * TT::NCH; ch += TT::NW) {
+      const int v = ch / TT::NCH, u = (ch % TT::NCH) * 10 + col;
+      const bool ok = col < 10 && u <= 2 * n1 && v <= ((L::D == 3) ? 2 * n2 : 0);
+      float f1[Q], drho = 0.0f, dux = 0.0f, duy = 0.0f, duz = 0.0f;
+      if (ok) {
+        int x1 = 2 * r1 - 1 + u, x2 = (L::D == 3) ? 2 * r2 - 1 + v : 0;
+        if (pick(c.per, t1)) x1 = wrapi(x1, pick(c.n, t1));
+        if (L::D == 3 && pick(c.per, t2)) x2 = wrapi(x2, pick(c.n, t2));
+        auto co = [&](int b) { return b == a ? xa : (b == t1 ? x1 : x2); };
+        float g[Q];
+        load_pre<L, S>(fcb, c.plane, node_addr<L>(c, co(0), co(1), co(2)), cpar, c.es, g);
+        split_neq<L>(g, ref, drho, dux, duy, duz, f1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f1[i] *= w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f1[i] = 0.0f;
+      }
+      // lane 3 col gets (d = -1) + (d = 0) + (d = +1) of its column
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const float s0 = __shfl_down_sync(0xffffffffu, f1[i], 1);
+        const float s1 = __shfl_down_sync(0xffffffffu, f1[i], 2);
+        if (ok && d == -1) A[i][v][u] = (f1[i] + s0) + s1;
+      }
+      if (ok && d == 0 && (u & 1) && (L::D == 2 || (v & 1))) {
+        const int j = (L::D == 3) ? (v - 1) >> 1 : 0, i = (u - 1) >> 1;
+        cm[j][i][0] = drho;
+        cm[j][i][1] = dux;
+        cm[j][i][2] = duy;
+        cm[j][i][3] = duz;
+      }
+    }
+  }
+  __syncthreads();
+  // 2. filter along t1 and t2: TN node (i, j) sits at footprint column
+  // (2 i + 1, 2 j + 1)
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int e = tid; e < Q * TI * TJ; e += TT::NT) {
+    const int i = e % TI, j = (e / TI) % TJ, q = e / (TI * TJ);
+    if (i >= n1 || j >= n2) continue;
+    float s;
+    if constexpr (L::D == 3) {
+      s = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float* row = &A[q][2 * j + b][2 * i];
+        const float rs = 0.25f * row[0] + 0.5f * row[1] + 0.25f * row[2];
+        s += (b == 1 ? 0.5f : 0.25f) * rs;
+      }
+    } else {
+      const float* row = &A[q][0][2 * i];
+      s = 0.25f * row[0] + 0.5f * row[1] + 0.25f * row[2];
+    }
+    Cf[q][j][i] = s;
+  }
+  __syncthreads();
+  // 3. rebuild f = f0(rho, u) + resc f^(1) (eq. rescfc) and store for the
+  // parent's update of parity ppar
+  const int node = tid % TT::NN, grp = tid / TT::NN;
+  const int i = node % TI, j = node / TI;
+  if (grp >= TT::G || i >= n1 || j >= n2) return;
+  // parent coordinates: box-relative + lo on axes the box spans
+  auto pc = [&](int b) {
+    int r = b == a ? ra : (b == t1 ? r1 + i : ((L::D == 3) ? r2 + j : 0));
+    if (pick(T.boxed, b)) {
+      r += pick(T.lo, b);
+      if (pick(p.per, b)) r = wrapi(r, pick(p.n, b));
+    }
+    return r;
+  };
+  const float drho = cm[j][i][0], dux = cm[j][i][1], duy = cm[j][i][2];
+  const float duz = (L::D == 3) ? cm[j][i][3] : 0.0f;
+  const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;
+  const float ux = Ux + dux, uy = Uy + duy, uz = Uz + duz;
+  float Ac[7], dA[7];
+  third_coeffs(ux, uy, uz, dux, duy, duz, Ux, Uy, Uz, Ac, dA);
+  const float dusq = 1.5f * (dux * (ux + Ux) + duy * (uy + Uy) + duz * (uz + Uz));
+  const float rho = ref.rho0 + drho;
+  S* fp = run_ptr<S>(p, run);
+  const NodeAddr ad = node_addr<L>(p, pc(0), pc(1), pc(2));
+  sfor<Q>([&](auto I) {
+    constexpr int q = decltype(I)::value;
+    if (q % TT::G == grp) {
+      const float g = eq_i<L, q, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
+                      resc * Cf[q][j][i];
+      store_pre_i<L, S, q>(fp, p.plane, ad, ppar, p.es, g);
+    }
+  });
 }
 
 // ------------------------------------------------------ set-up / read-out

@@ -164,6 +164,18 @@ cudaError_t inject(const LevelView& c, const BndDesc& B, const RingDesc& R, int 
     J.tstart[f + 1] = J.tstart[f] + (long long)J.ntile1[f] * J.ntile2[f];
   }
   dim3 grid((unsigned)J.tstart[J.nf], c.batch);
+  if constexpr (L::D == 3) {
+    dim3 block(T::TI, T::TJ);
+    if (storage == 0)
+      k_inject_sep<L, float><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0],
+                                                    slots[1], slots[2], resc, par,
+                                                    make_ref_f<L>(ref));
+    else
+      k_inject_sep<L, __half><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0],
+                                                     slots[1], slots[2], resc, par,
+                                                     make_ref_f<L>(ref));
+    return cudaGetLastError();
+  }
   dim3 block(T::TI, T::TJ, T::G);
   if (storage == 0)
     k_inject<L, float><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0], slots[1],
@@ -178,15 +190,29 @@ template <class L>
 cudaError_t restrict_tn(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
                         float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s) {
   if (T.count == 0) return cudaSuccess;
-  dim3 block(TnShape<L>::NB, TnShape<L>::M);
-  dim3 grid(blocks_for(T.count, TnShape<L>::M), p.batch);
+  using TT = RstTile<L>;
+  RstDesc J{};
+  J.tstart[0] = 0;
+  for (int f = 0; f < T.nf; ++f) {
+    const int a = T.axis[f];
+    if (L::D == 2) {
+      J.t1[f] = 1 - a;
+      J.t2[f] = 2;
+    } else {
+      J.t1[f] = (a == 0) ? 1 : 0;
+      J.t2[f] = (a == 2) ? 1 : 2;
+    }
+    J.ntile1[f] = (T.rext[f][J.t1[f]] + TT::TI - 1) / TT::TI;
+    const int nt2 = (T.rext[f][J.t2[f]] + TT::TJ - 1) / TT::TJ;
+    J.tstart[f + 1] = J.tstart[f] + (long long)J.ntile1[f] * nt2;
+  }
+  dim3 block(32, TT::NW);
+  dim3 grid((unsigned)J.tstart[T.nf], p.batch);
   const RefF R = make_ref_f<L>(ref);
   if (storage == 0)
-    k_restrict<L, float, false, false><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, R,
-                                                              nullptr, 0.0f, 1.0f, 0.0f);
+    k_restrict_tile<L, float><<<grid, block, 0, s>>>(p, c, T, J, resc, ppar, cpar, R);
   else
-    k_restrict<L, __half, false, false><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, R,
-                                                               nullptr, 0.0f, 1.0f, 0.0f);
+    k_restrict_tile<L, __half><<<grid, block, 0, s>>>(p, c, T, J, resc, ppar, cpar, R);
   return cudaGetLastError();
 }
 
