@@ -739,12 +739,16 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
 // (every thread the same four taps, even child positions weighting their
 // co-located parent node by one), then each node interpolates along t2 (a
 // warp holds one child row, so one or four taps uniformly) and rebuilds.
+#ifndef INJ_SEP_UNROLL
+#define INJ_SEP_UNROLL 4
+#endif
 template <class L>
 struct InjSep {
   static constexpr int TI = InjTile<L>::TI, TJ = InjTile<L>::TJ;
   static constexpr int WI = TI / 2 + 3, WJ = TJ / 2 + 3;
   static constexpr int NV = 4 + L::Q;
   static constexpr int NT = TI * TJ;
+  static constexpr int UNR = INJ_SEP_UNROLL;  // staging loop unroll
 };
 
 template <class L, class S>
@@ -775,7 +779,7 @@ __global__ void __launch_bounds__(InjSep<L>::NT)
   const long long K = R.K, nv = R.nv;
   const int tid = threadIdx.y * T::TI + threadIdx.x;
   // stage (eq. TempInt)
-#pragma unroll 4
+#pragma unroll(T::UNR)
   for (int e = tid; e < T::NV * T::WJ * T::WI; e += T::NT) {
     const int pi = e % T::WI, pj = (e / T::WI) % T::WJ, vv = e / (T::WI * T::WJ);
     int ri = p0i + pi, rj = p0j + pj;
@@ -1010,8 +1014,11 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
 #ifndef RST_TJ_3D
 #define RST_TJ_3D 4
 #endif
+#ifndef RST_NW_3D
+#define RST_NW_3D (2 * RST_TJ_3D + 1)
+#endif
 #ifndef RST_MINB_3D
-#define RST_MINB_3D 3
+#define RST_MINB_3D (27 / RST_NW_3D)
 #endif
 template <class L>
 struct RstTile {
@@ -1020,7 +1027,7 @@ struct RstTile {
   static constexpr int FI = 2 * TI + 1;                 // footprint columns along t1
   static constexpr int FJ = (L::D == 3) ? 2 * TJ + 1 : 1;
   static constexpr int NCH = (FI + 9) / 10;             // ten-column chunks per footprint row
-  static constexpr int NW = (L::D == 3) ? FJ : 3;       // warps
+  static constexpr int NW = (L::D == 3) ? RST_NW_3D : 3;  // warps
   static constexpr int NT = 32 * NW;
   static constexpr int NN = TI * TJ;                    // TN nodes per tile
   static constexpr int G = NT / NN;                     // threads per TN node in the rebuild
