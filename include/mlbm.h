@@ -149,7 +149,8 @@ int lbm_level_info(lbm_handle h, int level, int* n, double* tau,
 /* Set every node of one level of one run to the equilibrium f^(0)(rho, u)
  * (eq. fEqH; initial populations carry no off-equilibrium part).
  * rho: host [N] doubles; u: host [3][N] doubles (u[2] ignored in 2D).
- * Synchronises on the handle's stream. */
+ * Synchronises on the handle's stream.  Its device buffer (4 N doubles) is
+ * kept for the next lbm_init until every level of every run is set. */
 int lbm_init(lbm_handle h, int level, int run, const double* rho,
              const double* u);
 
@@ -191,7 +192,9 @@ int lbm_set_graphs(lbm_handle h, int enable);
 
 /* Macroscopic density and velocity of one level of one run, from the
  * post-collision state after the last step: rho host [N], u host [3][N]
- * (u[2] = 0 in 2D); NaN at inactive nodes.  Synchronises. */
+ * (u[2] = 0 in 2D); NaN at inactive nodes.  Synchronises.  The device
+ * buffer it converts into (4 N doubles) is kept for further read-outs
+ * (lbm_macros, lbm_populations) until the next lbm_step or lbm_destroy. */
 int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u);
 
 /* Same as lbm_macros but into device buffers (float): rho_dev [N],
@@ -201,7 +204,8 @@ int lbm_macros_device(lbm_handle h, int level, int run, float* rho_dev,
 
 /* Post-collision populations of one level of one run, shifted by the rest
  * state (f_i - w_i rho0, whatever u_ref is), host [q][N] doubles, in the
- * library's velocity order (returned by lbm_lattice).  Synchronises. */
+ * library's velocity order (returned by lbm_lattice).  Synchronises; keeps
+ * its device buffer like lbm_macros. */
 int lbm_populations(lbm_handle h, int level, int run, double* g);
 
 /* The library's velocity set: xi host [q][3] ints, w host [q] doubles.
@@ -210,14 +214,28 @@ int lbm_lattice(int lattice, int* xi, double* w);
 
 /* Register probe nodes: n nodes of `level`, ijk host [n][3] node indices.
  * After every coarse step the density and velocity of each probe of each
- * run are recorded on the device (capacity: 65536 coarse steps; older
- * samples are overwritten).  Replaces any earlier probe set. */
+ * run are recorded on the device (capacity: min(65536, max(16, 2^26 /
+ * (batch * n * 4))) coarse steps; older samples are overwritten).  Replaces
+ * any earlier probe set. */
 int lbm_probe_add(lbm_handle h, int level, int n, const int* ijk);
 
 /* Drain the probe record: out host [n_steps][batch][n][4] doubles
  * (rho, u_x, u_y, u_z), oldest first, at most max_steps; *n_steps receives
  * the number of recorded steps returned.  Synchronises. */
 int lbm_probe(lbm_handle h, double* out, int max_steps, int* n_steps);
+
+/* Asynchronous form of lbm_probe for a loop that reads every step's samples
+ * without stalling the device: enqueues, on the handle's stream after the
+ * work issued so far, the copies of the newest min(pending, max_steps)
+ * recorded steps into out (same layout as lbm_probe) and the reset of the
+ * record, and returns at once with that count in *n_steps.  "Pending" is
+ * counted on the host: one record per coarse step issued by lbm_step since
+ * the last read-out or lbm_probe_add (at most the record's capacity).
+ * out is owned by the caller and must stay valid, untouched, until
+ * lbm_sync(h) (or any synchronising call) returns; pinned host memory lets
+ * the copies overlap the following steps (pageable memory works but the
+ * driver may stage the copy synchronously).  Does not allocate. */
+int lbm_probe_async(lbm_handle h, double* out, int max_steps, int* n_steps);
 
 /* FP64 conservation diagnostics of one run, reduced on the device in a fixed
  * order (deterministic): per level, mass[l] = sum over active nodes of

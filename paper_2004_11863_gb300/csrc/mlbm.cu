@@ -168,6 +168,7 @@ struct lbm_ctx {
   }
   // probes
   int probe_level = -1, probe_n = 0, probe_cap = 0;
+  long long probe_pending = 0;  // coarse steps recorded since the last read-out
   int* probe_ijk = nullptr;
   double* probe_rec = nullptr;
   unsigned long long* probe_counter = nullptr;
@@ -188,6 +189,29 @@ struct lbm_ctx {
       alloc.free(p, alloc.user);
     else
       cudaFree(p);
+  }
+
+  // Device scratch of the synchronising set-up and read-out calls
+  // (lbm_init, lbm_macros, lbm_populations): kept from one such call to the
+  // next so that a loop over levels and runs allocates once; released when
+  // the last lbm_init completes the set-up, by the next lbm_step and by
+  // lbm_destroy.  Grows by
+  // freeing before allocating, so it never holds more than the largest
+  // single request.  Every user synchronises before returning, so the
+  // buffer is idle whenever it is released.
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  void* scratch_get(size_t bytes) {
+    if (scratch && bytes <= scratch_bytes) return scratch;
+    scratch_drop();
+    scratch = dalloc(bytes);
+    scratch_bytes = scratch ? bytes : 0;
+    return scratch;
+  }
+  void scratch_drop() {
+    dfree(scratch);
+    scratch = nullptr;
+    scratch_bytes = 0;
   }
 };
 
@@ -225,6 +249,7 @@ void release(lbm_ctx* h) {
   h->dfree(h->probe_ijk);
   h->dfree(h->probe_rec);
   h->dfree(h->probe_counter);
+  h->scratch_drop();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int l = 0; l < LBM_MAX_LEVELS; ++l) {
     if (h->side[l]) cudaStreamDestroy(h->side[l]);
@@ -863,7 +888,7 @@ int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* 
   }
   Level& v = h->lev[level];
   const long long N = v.n_nodes;
-  double* d = (double*)h->dalloc(sizeof(double) * 4 * N);
+  double* d = (double*)h->scratch_get(sizeof(double) * 4 * N);
   if (!d) return LBM_ENOMEM;
   int rc = LBM_OK;
   do {
@@ -880,10 +905,10 @@ int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* 
     }
     ++h->launches;
   } while (0);
-  h->dfree(d);
   if (rc) return rc;
   h->inited[(size_t)level * h->batch + run] = 1;
   if (std::all_of(h->inited.begin(), h->inited.end(), [](char c) { return c != 0; })) {
+    h->scratch_drop();  // set-up done: hold no more than the run itself
     for (int l = 0; l < h->nlev; ++l) {
       h->lev[l].last = 0;
       h->lev[l].nsteps = 0;
@@ -1009,6 +1034,7 @@ int lbm_set_graphs(lbm_handle h, int enable) {
 int lbm_step(lbm_handle h, int n_coarse) {
   if (!h || n_coarse < 0) return LBM_EINVAL;
   if (!h->ready) return LBM_ESTATE;
+  h->scratch_drop();
   if (!h->seeded) {
     int rc = seed_history(h);
     if (rc) return rc;
@@ -1050,6 +1076,7 @@ int lbm_step(lbm_handle h, int n_coarse) {
       h->launches += h->exec_nodes[key];
     }
     ++h->coarse_steps;
+    if (h->probe_n > 0) ++h->probe_pending;
   }
   return LBM_OK;
 }
@@ -1060,7 +1087,7 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
   if (!h->ready) return LBM_ESTATE;
   const Level& v = h->lev[level];
   const long long N = v.n_nodes;
-  double* d = (double*)h->dalloc(sizeof(double) * 4 * N);
+  double* d = (double*)h->scratch_get(sizeof(double) * 4 * N);
   if (!d) return LBM_ENOMEM;
   cudaError_t e = h->ops.macros_d(v.view, h->cfg.storage, run, v.last, d, d + N, h->ref,
                                   h->stream);
@@ -1070,7 +1097,6 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(u, d + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  h->dfree(d);
   if (e != cudaSuccess) {
     snprintf(g_errmsg, sizeof(g_errmsg), "macros: %s", cudaGetErrorString(e));
     return LBM_ECUDA;
@@ -1236,13 +1262,12 @@ int lbm_populations(lbm_handle h, int level, int run, double* g) {
   if (!h->ready) return LBM_ESTATE;
   const Level& v = h->lev[level];
   const size_t bytes = sizeof(double) * h->q * (size_t)v.n_nodes;
-  double* d = (double*)h->dalloc(bytes);
+  double* d = (double*)h->scratch_get(bytes);
   if (!d) return LBM_ENOMEM;
   cudaError_t e = h->ops.populations(v.view, h->cfg.storage, run, v.last, d, h->ref, h->stream);
   ++h->launches;
   if (e == cudaSuccess) e = cudaMemcpyAsync(g, d, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  h->dfree(d);
   if (e != cudaSuccess) {
     snprintf(g_errmsg, sizeof(g_errmsg), "populations: %s", cudaGetErrorString(e));
     return LBM_ECUDA;
@@ -1266,6 +1291,7 @@ int lbm_probe_add(lbm_handle h, int level, int n, const int* ijk) {
   h->probe_rec = nullptr;
   h->probe_counter = nullptr;
   h->probe_n = 0;
+  h->probe_pending = 0;
   if (n == 0) return LBM_OK;
   long long per_step = (long long)h->batch * n * 4;
   long long cap = std::min<long long>(65536, std::max<long long>(16, (1LL << 26) / per_step));
@@ -1300,6 +1326,31 @@ int lbm_probe(lbm_handle h, double* out, int max_steps, int* n_steps) {
   }
   CK(cudaMemsetAsync(h->probe_counter, 0, sizeof(unsigned long long), h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->probe_pending = 0;
+  *n_steps = (int)take;
+  return LBM_OK;
+}
+
+int lbm_probe_async(lbm_handle h, double* out, int max_steps, int* n_steps) {
+  if (!h || !n_steps || max_steps < 0 || (max_steps > 0 && !out)) return LBM_EINVAL;
+  *n_steps = 0;
+  if (h->probe_n <= 0) return LBM_OK;
+  // the device counter advanced once per coarse step since its last reset,
+  // so the host count gives the slots without reading it back
+  const long long kept = std::min<long long>(h->probe_pending, h->probe_cap);
+  const long long take = std::min<long long>(kept, max_steps);
+  const long long per_step = (long long)h->batch * h->probe_n * 4;
+  long long s = 0;
+  while (s < take) {  // at most two copies: the ring may wrap once
+    const long long step = h->probe_pending - take + s;
+    const long long slot = step % h->probe_cap;
+    const long long run = std::min<long long>(take - s, h->probe_cap - slot);
+    CK(cudaMemcpyAsync(out + s * per_step, h->probe_rec + slot * per_step,
+                       sizeof(double) * per_step * run, cudaMemcpyDeviceToHost, h->stream));
+    s += run;
+  }
+  CK(cudaMemsetAsync(h->probe_counter, 0, sizeof(unsigned long long), h->stream));
+  h->probe_pending = 0;
   *n_steps = (int)take;
   return LBM_OK;
 }

@@ -94,6 +94,7 @@ def lib():
     L.lbm_lattice.argtypes = [ctypes.c_int, ip, dp]
     L.lbm_probe_add.argtypes = [P, ctypes.c_int, ctypes.c_int, ip]
     L.lbm_probe.argtypes = [P, dp, ctypes.c_int, ip]
+    L.lbm_probe_async.argtypes = [P, dp, ctypes.c_int, ip]
     L.lbm_diag.argtypes = [P, ctypes.c_int, dp, dp]
     L.lbm_diag_noalloc.argtypes = [P, ctypes.c_int, dp, dp]
     L.lbm_bytes.argtypes = [ctypes.POINTER(lbm_config), ctypes.POINTER(ctypes.c_ulonglong)]
@@ -340,6 +341,21 @@ class Lbm:
         ns = ctypes.c_int()
         _check(lib().lbm_probe(self._h, _dp(out), max_steps, ctypes.byref(ns)), "lbm_probe")
         return out[: ns.value, :, :n]
+
+    def probe_async(self, out):
+        """Enqueue the read-out of the newest recorded probe steps into
+        `out`, a C-contiguous float64 array [k, batch, n, 4] (pinned host
+        memory for overlap); returns the number of steps that will land in
+        out[:count] once the stream reaches them (after sync()).  `out` must
+        stay alive and untouched until then."""
+        n = getattr(self, "_nprobe", 0)
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.ndim != 4 \
+                or out.shape[1:] != (self.batch, max(n, 1), 4):
+            raise ValueError("probe_async needs a C-contiguous float64 [k, batch, n, 4] array")
+        ns = ctypes.c_int()
+        _check(lib().lbm_probe_async(self._h, _dp(out), out.shape[0], ctypes.byref(ns)),
+               "lbm_probe_async")
+        return ns.value
 
     def diag(self, run=0):
         mass = np.zeros(self.nlevels)
