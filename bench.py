@@ -341,15 +341,20 @@ def main():
     for l in range(case.nlevels):
         for b in range(batch):
             g.init(l, b, fields[l][0].numpy(), fields[l][1].numpy())
+    t_init = time.perf_counter()
     d2h_probe = 0
     for k in range(args.steps):
         g.step(1)
         got = g.probe_async(recn[k:k + 1])
         d2h_probe += got * recn[k].nbytes
+    g.sync()
+    t_steps = time.perf_counter()
     for l in range(case.nlevels):
         for b in range(batch):
             g.macros(l, b)
     e2e_s = time.perf_counter() - t0
+    phases = {"init_s": round(t_init - t0, 4), "steps_s": round(t_steps - t_init, 4),
+              "readout_s": round(t0 + e2e_s - t_steps, 4)}
     if not np.all(np.isfinite(recn)):
         raise RuntimeError("probe record not finite after the end-to-end run")
     h2d = sum(4 * fields[l][0].numel() * 8 for l in range(case.nlevels)) * batch
@@ -359,7 +364,8 @@ def main():
            "note": f"lbm_init of every level and run from pinned host fields, then {args.steps} x "
                    f"(lbm_step 1 + lbm_probe_async read-back of that step's 16 probes x {batch} "
                    f"runs into pinned host memory, enqueued behind the step), then lbm_macros of "
-                   f"every level and run (synchronising); bytes amortised per step"}
+                   f"every level and run (synchronising); bytes amortised per step",
+           "phases": phases}
     g.close()
 
     # ---------------- variants of the same workload (same batch) ------------
