@@ -332,16 +332,35 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
   }
 }
 
-// Level update of binary32 storage, two nodes per thread in one two-lane
-// collision: the nodes (x, y0) and (x, y0 + 1) take the two lanes of the
-// packed FP32 arithmetic (lattice_x2.cuh), so their collisions issue about
-// half the floating-point instructions of two scalar collisions.  A lane
-// whose node is outside the level or inactive computes on its partner's
-// populations and stores nothing.  Per lattice, K1X2_<lattice> selects this
-// kernel over k_stream_collide for binary32 and K1X2_MINB_<lattice> the
-// resident blocks per SM it is compiled for.
+// Level update, two nodes per thread in one two-lane collision: the nodes
+// (x, y0) and (x, y0 + 1) take the two lanes of the packed FP32 arithmetic
+// (lattice_x2.cuh), so their collisions issue about half the floating-point
+// instructions of two scalar collisions.  A lane whose node is outside the
+// level or inactive computes on its partner's populations and stores
+// nothing.  Per lattice, K1X2_<lattice> selects this kernel over
+// k_stream_collide for binary32, K1X2H_<lattice> for binary16 with one run
+// per element (es = 1), and K1X2_MINB_<lattice> / K1X2H_MINB_<lattice> set
+// the resident blocks per SM each is compiled for.
+#ifndef K1X2H_D2Q9
+#define K1X2H_D2Q9 1
+#endif
+#ifndef K1X2H_D3Q19
+#define K1X2H_D3Q19 1
+#endif
+#ifndef K1X2H_D3Q27
+#define K1X2H_D3Q27 1
+#endif
 #ifndef K1X2_D2Q9
 #define K1X2_D2Q9 0
+#endif
+#ifndef K1X2H_MINB_D2Q9
+#define K1X2H_MINB_D2Q9 K1X2_MINB_D2Q9
+#endif
+#ifndef K1X2H_MINB_D3Q19
+#define K1X2H_MINB_D3Q19 K1X2_MINB_D3Q19
+#endif
+#ifndef K1X2H_MINB_D3Q27
+#define K1X2H_MINB_D3Q27 K1X2_MINB_D3Q27
 #endif
 #ifndef K1X2_D3Q19
 #define K1X2_D3Q19 1
@@ -363,21 +382,28 @@ struct K1X2Tune;
 template <>
 struct K1X2Tune<D2Q9> {
   static constexpr bool ON = K1X2_D2Q9;
+  static constexpr bool ON_H = K1X2H_D2Q9;
   static constexpr int MINB = K1X2_MINB_D2Q9;
+  static constexpr int MINB_H = K1X2H_MINB_D2Q9;
 };
 template <>
 struct K1X2Tune<D3Q19> {
   static constexpr bool ON = K1X2_D3Q19;
+  static constexpr bool ON_H = K1X2H_D3Q19;
   static constexpr int MINB = K1X2_MINB_D3Q19;
+  static constexpr int MINB_H = K1X2H_MINB_D3Q19;
 };
 template <>
 struct K1X2Tune<D3Q27> {
   static constexpr bool ON = K1X2_D3Q27;
+  static constexpr bool ON_H = K1X2H_D3Q27;
   static constexpr int MINB = K1X2_MINB_D3Q27;
+  static constexpr int MINB_H = K1X2H_MINB_D3Q27;
 };
 
-template <class L, int COLL, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, K1X2Tune<L>::MINB)
+template <class L, class S, int COLL, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
+                                                                      : K1X2Tune<L>::MINB_H)
     k_stream_collide_x2(LevelView v, float omega, RefF R) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
@@ -390,29 +416,37 @@ __global__ void __launch_bounds__(128, K1X2Tune<L>::MINB)
   const bool ok0 = y0 < v.n[1] && !inactive(v, x, y0, z);
   const bool ok1 = y0 + 1 < v.n[1] && !inactive(v, x, y0 + 1, z);
   if (!ok0 && !ok1) return;
-  float* f = static_cast<float*>(v.f) + run * v.run_stride;  // es = 1 for binary32
+  S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
   // each lane's node; an idle lane reads its partner's
   const NodeAddr a0 = node_addr<L>(v, x, ok0 ? y0 : y0 + 1, z);
   const NodeAddr a1 = node_addr<L>(v, x, ok1 ? y0 + 1 : y0, z);
+  // element offsets are formed whole before indexing (f[i * plane + at]):
+  // per-direction base pointers would cost 64-bit registers per direction
   F2 g[L::Q];
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (PAR == 0) {
-      g[i].v.x = f[(long long)i * v.plane + a0.at(0, 0, 0)];
-      g[i].v.y = f[(long long)i * v.plane + a1.at(0, 0, 0)];
+      g[i].v.x = Store<S>::ld(&f[(long long)i * v.plane + a0.at(0, 0, 0)]);
+      g[i].v.y = Store<S>::ld(&f[(long long)i * v.plane + a1.at(0, 0, 0)]);
     } else {
-      g[i].v.x = f[(long long)opp<L>(i) * v.plane + a0.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))];
-      g[i].v.y = f[(long long)opp<L>(i) * v.plane + a1.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))];
+      g[i].v.x = Store<S>::ld(
+          &f[(long long)opp<L>(i) * v.plane + a0.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
+      g[i].v.y = Store<S>::ld(
+          &f[(long long)opp<L>(i) * v.plane + a1.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
     }
   });
   collide_emit_x2<L, COLL, MOV>(g, omega, R, [&](auto I, F2 val) {
     constexpr int i = decltype(I)::value;
     if constexpr (PAR == 0) {
-      if (ok0) f[(long long)opp<L>(i) * v.plane + a0.at(0, 0, 0)] = val.v.x;
-      if (ok1) f[(long long)opp<L>(i) * v.plane + a1.at(0, 0, 0)] = val.v.y;
+      if (ok0) Store<S>::st(&f[(long long)opp<L>(i) * v.plane + a0.at(0, 0, 0)], val.v.x);
+      if (ok1) Store<S>::st(&f[(long long)opp<L>(i) * v.plane + a1.at(0, 0, 0)], val.v.y);
     } else {
-      if (ok0) f[(long long)i * v.plane + a0.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))] = val.v.x;
-      if (ok1) f[(long long)i * v.plane + a1.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))] = val.v.y;
+      if (ok0)
+        Store<S>::st(&f[(long long)i * v.plane + a0.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))],
+                     val.v.x);
+      if (ok1)
+        Store<S>::st(&f[(long long)i * v.plane + a1.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))],
+                     val.v.y);
     }
   });
 }

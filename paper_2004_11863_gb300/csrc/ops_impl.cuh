@@ -33,7 +33,7 @@ RefF make_ref_f(const RefState& r) {
   return R;
 }
 
-template <class L, int COLL>
+template <class L, class S, int COLL>
 cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx,
                          int by, cudaStream_t s) {
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
@@ -43,14 +43,14 @@ cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefStat
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
     if (par == 0)
-      k_stream_collide_x2<L, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R);
     else
-      k_stream_collide_x2<L, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R);
   } else {
     if (par == 0)
-      k_stream_collide_x2<L, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R);
     else
-      k_stream_collide_x2<L, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R);
   }
   return cudaGetLastError();
 }
@@ -58,8 +58,9 @@ cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefStat
 template <class L, class S, int COLL>
 cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx, int by,
                       cudaStream_t s) {
-  if constexpr (std::is_same<S, float>::value && K1X2Tune<L>::ON)
-    return sc_x2_launch<L, COLL>(v, par, omega, ref, bx, by, s);
+  if constexpr ((std::is_same<S, float>::value && K1X2Tune<L>::ON) ||
+                (std::is_same<S, __half>::value && K1X2Tune<L>::ON_H))
+    return sc_x2_launch<L, S, COLL>(v, par, omega, ref, bx, by, s);
   constexpr int NPT = K1Tune<L, S>::NPT;
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);

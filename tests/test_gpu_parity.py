@@ -51,6 +51,12 @@ CASES_2D = [
                                      [((20, 18, 0), (60, 54, 1))],
                                      dict(kind="pulse", center=(12.0, 36.0, 0.0), radius=4.0,
                                           amplitude=1e-3), 40)),
+    # a fine band spanning the periodic x axis: the interface faces are
+    # normal to y and their tiles wrap around x
+    ("band2d", lambda: W.Case("band2d", "D2Q9", "RR", 0.52, (70, 48, 1),
+                              [((0, 12, 0), (70, 36, 1))],
+                              dict(kind="vortex", u0=(0.0, 0.1 * W.CS, 0.0),
+                                   center=(66.0, 16.0, 0.0), radius=4.0, eps=0.05 * W.CS), 30)),
 ]
 
 
@@ -71,6 +77,12 @@ CASES_3D = [
     ("d3q27_2lev_reg", lambda: W.small_3d("D3Q27", "REG", nlevels=2, steps=4)),
     ("d3q27_3lev_rr", lambda: W.small_3d("D3Q27", "RR", nlevels=3, steps=3)),
     ("d3q19_slab", lambda: W.slab_small_3d("D3Q19", "RR", steps=5)),
+    # a fine tube along the periodic x axis: faces normal to y and z, tiles
+    # wrapping around x, 29 TN nodes per face row (two ragged tiles)
+    ("d3q27_tube", lambda: W.Case("tube3d", "D3Q27", "RR", 0.52, (29, 16, 17),
+                                  [((0, 4, 4), (29, 12, 13))],
+                                  dict(kind="pulse", center=(27.0, 6.0, 8.0), radius=3.0,
+                                       amplitude=1e-3, u0=(0.05, 0.0, 0.0)), 4)),
 ]
 
 
