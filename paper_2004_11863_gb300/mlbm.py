@@ -281,10 +281,19 @@ class Lbm:
     def set_graphs(self, enable: bool):
         _check(lib().lbm_set_graphs(self._h, int(bool(enable))), "lbm_set_graphs")
 
-    def macros(self, level, run=0):
+    def macros(self, level, run=0, out=None):
+        """lbm_macros: (rho [N], u [3, N]) float64.  out: optional
+        caller-owned (rho, u) arrays of those shapes, C-contiguous float64
+        (pinned host memory makes the copy faster), filled and returned."""
         N = self.nodes(level)
-        rho = np.empty(N)
-        u = np.empty((3, N))
+        if out is None:
+            rho = np.empty(N)
+            u = np.empty((3, N))
+        else:
+            rho, u = out
+            for a, shp in ((rho, (N,)), (u, (3, N))):
+                if a.dtype != np.float64 or a.shape != shp or not a.flags.c_contiguous:
+                    raise ValueError(f"macros out arrays must be C-contiguous float64 {shp}")
         _check(lib().lbm_macros(self._h, level, run, _dp(rho), _dp(u)), "lbm_macros")
         return rho, u
 

@@ -288,6 +288,26 @@ def test_probe_async_matches_probe(M):
     assert b.probe_async(out) == 0
 
 
+def test_macros_into_caller_buffers(M):
+    """lbm_macros into caller-owned (pinned) arrays returns the same bits
+    as into fresh arrays; wrong shapes are refused before any copy."""
+    import torch
+    case = W.small_3d("D3Q27", "RR", nlevels=2, steps=3)
+    g = M.Lbm.from_case(case, batch=2)
+    g.step(3)
+    for l in range(2):
+        N = g.nodes(l)
+        out = (torch.empty(N, dtype=torch.float64).pin_memory().numpy(),
+               torch.empty((3, N), dtype=torch.float64).pin_memory().numpy())
+        for run in range(2):
+            r0, u0 = g.macros(l, run)
+            r1, u1 = g.macros(l, run, out=out)
+            assert r1 is out[0] and u1 is out[1]
+            assert np.array_equal(r0, r1, equal_nan=True) and np.array_equal(u0, u1, equal_nan=True)
+    with pytest.raises(ValueError):
+        g.macros(0, 0, out=(np.empty(3), np.empty((3, 3))))
+
+
 def test_reflected_acoustic_wave_matches_oracle(M):
     """The GPU reproduces the oracle's reflected-wave ratio of the convected
     1D acoustic wave (Sec. 9.2) and its fields within 1e-6."""
