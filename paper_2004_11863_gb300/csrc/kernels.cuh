@@ -12,10 +12,8 @@
 //                     in 3D);
 //   k_restrict_tile   parent TN nodes: filtered child f^(1) (eq. filterFneq),
 //                     rescaling (eq. rescfc), written where the parent's next
-//                     update reads them (the restriction), per face tile
-//                     (k_restrict: one thread per TN node and filter
-//                     neighbour, kept for the hybrid collision, which also
-//                     collides the TN nodes);
+//                     update reads them (the restriction), per face tile; with
+//                     the hybrid collision it also collides the TN nodes;
 //   k_init / k_macros / k_diag_* / k_probe   set-up and read-out.
 //
 // AA pattern.  A step of parity 0 reads g_i of node n from plane i at n and
@@ -903,135 +901,7 @@ __device__ __forceinline__ void strain_from(const float (&up)[3][3], const float
 }
 
 // ----------------------------------------------------------- K4: restrict
-// Parent TN nodes.  resc = 2 tau_c / tau_f (eq. rescfc); ppar / cpar: the
-// parent's and the child's next updates.  A block handles kTnPerBlock TN
-// nodes with one thread per (TN node, filter neighbour): each thread forms
-// the weighted f^(1) of its child node, the block sums the 3^D neighbours in
-// a fixed order (so results do not depend on scheduling), and one thread per
-// TN node rebuilds and stores the populations.
-// HRR (hybrid collision): the rebuilt TN node is collided at once with
-// S = 2 S^f (eq. PijResc), S^f from central differences of the child
-// velocities at the co-located node's axis neighbours (among the filter
-// neighbours), and its post-collision state stored for the parent's update
-// of parity ppar (which skips TN nodes); its velocity deviation goes to the
-// parent's velocity planes pdu.
-template <class L>
-struct TnShape {
-  static constexpr int NB = (L::D == 3) ? 27 : 9;   // filter neighbours
-  static constexpr int M = (L::D == 3) ? 8 : 16;    // TN nodes per block
-};
-
-template <class L, class S, bool HRR, bool MOV>
-__global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
-    k_restrict(LevelView p, LevelView c, TnDesc T, float resc, int ppar, int cpar, RefF ref,
-               float* pdu, float omega_p, float sig, float ks_p) {
-  constexpr int NB = TnShape<L>::NB, M = TnShape<L>::M, Q = L::Q;
-  __shared__ float red[M][NB][Q];
-  __shared__ float cm[M][4];
-  __shared__ float cu[HRR ? M : 1][HRR ? NB : 1][3];
-  const int kn = threadIdx.x, m = threadIdx.y;
-  const long long k = (long long)blockIdx.x * M + m;
-  const int run = blockIdx.y;
-  const bool valid = k < T.count;
-  int P[3] = {0, 0, 0}, X[3] = {0, 0, 0};
-  if (valid) {
-    const int fc = ring_face(T.start, T.nf, k);
-    long long loc = k - T.start[fc];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int e = T.rext[fc][a];
-      const int r = T.rlo[fc][a] + (int)(loc % e);
-      loc /= e;
-      if (T.boxed[a]) {
-        int pc = T.lo[a] + r;
-        if (p.per[a]) pc = wrapi(pc, p.n[a]);
-        P[a] = pc;
-      } else {
-        P[a] = r;
-      }
-      X[a] = 2 * r;
-    }
-    const int dx = kn % 3 - 1, dy = (kn / 3) % 3 - 1, dz = (L::D == 3) ? kn / 9 - 1 : 0;
-    int xx = X[0] + dx, yy = X[1] + dy, zz = X[2] + dz;
-    if (c.per[0]) xx = wrapi(xx, c.n[0]);
-    if (c.per[1]) yy = wrapi(yy, c.n[1]);
-    if (L::D == 3 && c.per[2]) zz = wrapi(zz, c.n[2]);
-    const S* fcb = run_cptr<S>(c, run);
-    const NodeAddr a = node_addr<L>(c, xx, yy, zz);
-    float g[Q], f1[Q], drho, ux, uy, uz;  // (ux, uy, uz): velocity deviations
-    load_pre<L, S>(fcb, c.plane, a, cpar, c.es, g);
-    split_neq<L>(g, ref, drho, ux, uy, uz, f1);
-    const float w = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f) *
-                    (L::D == 3 ? (dz == 0 ? 0.5f : 0.25f) : 1.0f);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) red[m][kn][i] = w * f1[i];
-    if constexpr (HRR) {
-      cu[m][kn][0] = ux;
-      cu[m][kn][1] = uy;
-      cu[m][kn][2] = uz;
-    }
-    if (dx == 0 && dy == 0 && dz == 0) {
-      cm[m][0] = drho;
-      cm[m][1] = ux;
-      cm[m][2] = uy;
-      cm[m][3] = uz;
-    }
-  }
-  __syncthreads();
-  // fixed-order sum over the neighbours, one thread per population
-  if (valid && kn < Q) {
-    float s = 0.0f;
-    for (int n = 0; n < NB; ++n) s += red[m][n][kn];
-    red[m][0][kn] = s;  // row 0 was read by this thread only, first
-  }
-  __syncthreads();
-  if (valid && kn == 0) {
-    float g[Q];
-    equilibrium_f<L>(cm[m][0], cm[m][1], cm[m][2], cm[m][3], ref, g);
-    sfor<Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      g[i] += resc * red[m][0][i];
-    });
-    S* fp = run_ptr<S>(p, run);
-    const NodeAddr a = node_addr<L>(p, P[0], P[1], P[2]);
-    const int es = p.es;
-    if constexpr (HRR) {
-      float up[3][3] = {}, um[3][3] = {};
-      for (int ax = 0; ax < L::D; ++ax) {
-        const int ip = 13 - (L::D == 2 ? 9 : 0) + (ax == 0 ? 1 : ax == 1 ? 3 : 9);
-        const int im = 13 - (L::D == 2 ? 9 : 0) - (ax == 0 ? 1 : ax == 1 ? 3 : 9);
-        for (int b = 0; b < 3; ++b) {
-          up[ax][b] = cu[m][ip][b];
-          um[ax][b] = cu[m][im][b];
-        }
-      }
-      HrrIn hy;
-      hy.sig = sig;
-      hy.ks = ks_p;
-      strain_from<L>(up, um, hy.s);
-#pragma unroll
-      for (int j = 0; j < 6; ++j) hy.s[j] *= 2.0f;  // eq. PijResc
-      collide_emit<L, 3, MOV>(
-          g, omega_p, ref,
-          [&](auto I, float val) {
-            constexpr int i = decltype(I)::value;
-            if (ppar == 0)
-              Store<S>::st(fp + (long long)opp<L>(i) * p.plane + es * a.at(0, 0, 0), val);
-            else
-              Store<S>::st(fp + (long long)i * p.plane +
-                               es * a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2)),
-                           val);
-          },
-          &hy);
-      float* d = pdu + (long long)run * L::D * p.plane + a.at(0, 0, 0);
-      for (int b = 0; b < L::D; ++b) d[(long long)b * p.plane] = cm[m][1 + b];
-    } else {
-      store_pre<L, S>(fp, p.plane, a, ppar, es, g);
-    }
-  }
-}
-
-// Face-tiled restriction (plain and regularized collisions).  The filter of
+// Face-tiled restriction.  The filter of
 // eq. filterFneq is a tensor product of (1/4, 1/2, 1/4) along each axis, so
 // a block that owns TI x TJ TN nodes of one face first forms, for every
 // child node column of the tile's footprint (2 TI + 1 by 2 TJ + 1 columns
@@ -1045,6 +915,14 @@ __global__ void __launch_bounds__(TnShape<L>::NB * TnShape<L>::M)
 // normal to x one warp load fetches three neighbouring values per row
 // instead of one, and the column's sum is formed by two warp shuffles in a
 // fixed order.
+// HRR (hybrid collision): the tile also keeps the velocity deviations of
+// its children -- the centre node of every column and the two normal-axis
+// neighbours of every TN column -- so that S^f at the co-located child node
+// comes from central differences over its six axis neighbours; one thread
+// per TN node then collides the rebuilt node with S = 2 S^f (eq. PijResc),
+// stores its post-collision state for the parent's update of parity ppar
+// (which skips TN nodes) and writes its velocity deviation to the parent's
+// velocity planes pdu.
 #ifndef RST_TJ_3D
 #define RST_TJ_3D 4
 #endif
@@ -1066,18 +944,23 @@ struct RstTile {
   static constexpr int NN = TI * TJ;                    // TN nodes per tile
   static constexpr int G = NT / NN;                     // threads per TN node in the rebuild
   static constexpr int MINB = (L::D == 3) ? RST_MINB_3D : 8;  // resident blocks per SM
+  static constexpr int MINB_HRR = (L::D == 3) ? 2 : 6;         // ... with the collision
 };
 
-template <class L, class S>
-__global__ void __launch_bounds__(RstTile<L>::NT, RstTile<L>::MINB)
+template <class L, class S, bool HRR, bool MOV>
+__global__ void __launch_bounds__(RstTile<L>::NT, HRR ? RstTile<L>::MINB_HRR : RstTile<L>::MINB)
     k_restrict_tile(LevelView p, LevelView c, const __grid_constant__ TnDesc T,
                     const __grid_constant__ RstDesc J, float resc, int ppar, int cpar,
-                    RefF ref) {
+                    RefF ref, float* pdu, float omega_p, float sig, float ks_p) {
   using TT = RstTile<L>;
   constexpr int Q = L::Q, TI = TT::TI, TJ = TT::TJ, FI = TT::FI, FJ = TT::FJ;
   __shared__ float A[Q][FJ][FI];    // normal-filtered f^(1) per footprint column
   __shared__ float Cf[Q][TJ][TI];   // fully filtered f^(1) per TN node
   __shared__ float cm[TJ][TI][4];   // (drho, du) of the co-located child node
+  // HRR: du of every column's centre node, and of the normal neighbours
+  // (d = -1, +1) of every TN column
+  __shared__ float cu0[HRR ? 3 : 1][HRR ? FJ : 1][HRR ? FI : 1];
+  __shared__ float cun[HRR ? 2 : 1][HRR ? 3 : 1][HRR ? TJ : 1][HRR ? TI : 1];
   const int run = blockIdx.y;
   int f = 0;
   while (f + 1 < T.nf && (long long)blockIdx.x >= J.tstart[f + 1]) ++f;
@@ -1123,12 +1006,26 @@ __global__ void __launch_bounds__(RstTile<L>::NT, RstTile<L>::MINB)
         const float s1 = __shfl_down_sync(0xffffffffu, f1[i], 2);
         if (ok && d == -1) A[i][v][u] = (f1[i] + s0) + s1;
       }
-      if (ok && d == 0 && (u & 1) && (L::D == 2 || (v & 1))) {
+      const bool tn_col = (u & 1) && (L::D == 2 || (v & 1));
+      if (ok && d == 0 && tn_col) {
         const int j = (L::D == 3) ? (v - 1) >> 1 : 0, i = (u - 1) >> 1;
         cm[j][i][0] = drho;
         cm[j][i][1] = dux;
         cm[j][i][2] = duy;
         cm[j][i][3] = duz;
+      }
+      if constexpr (HRR) {
+        if (ok && d == 0) {
+          cu0[0][v][u] = dux;
+          cu0[1][v][u] = duy;
+          cu0[2][v][u] = duz;
+        }
+        if (ok && d != 0 && tn_col) {
+          const int j = (L::D == 3) ? (v - 1) >> 1 : 0, i = (u - 1) >> 1, k = d > 0;
+          cun[k][0][j][i] = dux;
+          cun[k][1][j][i] = duy;
+          cun[k][2][j][i] = duz;
+        }
       }
     }
   }
@@ -1169,6 +1066,56 @@ __global__ void __launch_bounds__(RstTile<L>::NT, RstTile<L>::MINB)
     }
     return r;
   };
+  if constexpr (HRR) {
+    if (grp != 0) return;
+    float g[Q];
+    equilibrium_f<L>(cm[j][i][0], cm[j][i][1], cm[j][i][2], cm[j][i][3], ref, g);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) g[q] += resc * Cf[q][j][i];
+    // S^f by central differences (child spacing) at the co-located node,
+    // whose footprint column is (2 i + 1, 2 j + 1)
+    const int u = 2 * i + 1, v = (L::D == 3) ? 2 * j + 1 : 0;
+    float up[3][3] = {}, um[3][3] = {};
+#pragma unroll
+    for (int ax = 0; ax < L::D; ++ax)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (ax == a) {
+          up[ax][b] = cun[1][b][j][i];
+          um[ax][b] = cun[0][b][j][i];
+        } else if (ax == t1) {
+          up[ax][b] = cu0[b][v][u + 1];
+          um[ax][b] = cu0[b][v][u - 1];
+        } else if constexpr (L::D == 3) {
+          up[ax][b] = cu0[b][v + 1][u];
+          um[ax][b] = cu0[b][v - 1][u];
+        }
+      }
+    HrrIn hy;
+    hy.sig = sig;
+    hy.ks = ks_p;
+    strain_from<L>(up, um, hy.s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) hy.s[k] *= 2.0f;  // eq. PijResc
+    S* fp = run_ptr<S>(p, run);
+    const NodeAddr ad = node_addr<L>(p, pc(0), pc(1), pc(2));
+    const int es = p.es;
+    collide_emit<L, 3, MOV>(
+        g, omega_p, ref,
+        [&](auto I, float val) {
+          constexpr int q = decltype(I)::value;
+          if (ppar == 0)
+            Store<S>::st(fp + (long long)opp<L>(q) * p.plane + es * ad.at(0, 0, 0), val);
+          else
+            Store<S>::st(fp + (long long)q * p.plane +
+                             es * ad.at(L::c(q, 0), L::c(q, 1), L::c(q, 2)),
+                         val);
+        },
+        &hy);
+    float* dp = pdu + (long long)run * L::D * p.plane + ad.at(0, 0, 0);
+    for (int b = 0; b < L::D; ++b) dp[(long long)b * p.plane] = cm[j][i][1 + b];
+    return;
+  }
   const float drho = cm[j][i][0], dux = cm[j][i][1], duy = cm[j][i][2];
   const float duz = (L::D == 3) ? cm[j][i][3] : 0.0f;
   const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;

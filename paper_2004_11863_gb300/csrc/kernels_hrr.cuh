@@ -19,7 +19,7 @@
 //                         interpolated in time (eq. TempInt) and space
 //                         (eq. spaceInt), halved (eq. PijResc), then the
 //                         collision;
-//   k_restrict<HRR>       (kernels.cuh) collides each rebuilt TN node at once
+//   k_restrict_tile<HRR>  (kernels.cuh) collides each rebuilt TN node at once
 //                         with S = 2 S^f of its co-located child node.
 //
 // Strain-rate history layout: sh[((run * 3 + slot) * 6 + j) * K + k],

@@ -187,10 +187,9 @@ cudaError_t inject(const LevelView& c, const BndDesc& B, const RingDesc& R, int 
   return cudaGetLastError();
 }
 
+// Face tiles of the TN nodes for k_restrict_tile.
 template <class L>
-cudaError_t restrict_tn(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
-                        float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s) {
-  if (T.count == 0) return cudaSuccess;
+RstDesc rst_desc(const TnDesc& T) {
   using TT = RstTile<L>;
   RstDesc J{};
   J.tstart[0] = 0;
@@ -207,13 +206,23 @@ cudaError_t restrict_tn(const LevelView& p, const LevelView& c, const TnDesc& T,
     const int nt2 = (T.rext[f][J.t2[f]] + TT::TJ - 1) / TT::TJ;
     J.tstart[f + 1] = J.tstart[f] + (long long)J.ntile1[f] * nt2;
   }
-  dim3 block(32, TT::NW);
+  return J;
+}
+
+template <class L>
+cudaError_t restrict_tn(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
+                        float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s) {
+  if (T.count == 0) return cudaSuccess;
+  const RstDesc J = rst_desc<L>(T);
+  dim3 block(32, RstTile<L>::NW);
   dim3 grid((unsigned)J.tstart[T.nf], p.batch);
   const RefF R = make_ref_f<L>(ref);
   if (storage == 0)
-    k_restrict_tile<L, float><<<grid, block, 0, s>>>(p, c, T, J, resc, ppar, cpar, R);
+    k_restrict_tile<L, float, false, false><<<grid, block, 0, s>>>(p, c, T, J, resc, ppar, cpar,
+                                                                   R, nullptr, 0.0f, 1.0f, 0.0f);
   else
-    k_restrict_tile<L, __half><<<grid, block, 0, s>>>(p, c, T, J, resc, ppar, cpar, R);
+    k_restrict_tile<L, __half, false, false><<<grid, block, 0, s>>>(
+        p, c, T, J, resc, ppar, cpar, R, nullptr, 0.0f, 1.0f, 0.0f);
   return cudaGetLastError();
 }
 
@@ -225,10 +234,11 @@ template <class L, class S, bool MOV>
 void restrict_hrr_t(const LevelView& p, const LevelView& c, const TnDesc& T, float resc, int ppar,
                     int cpar, float* pdu, float omega_p, float sig, float ks_p, const RefF& R,
                     cudaStream_t s) {
-  dim3 block(TnShape<L>::NB, TnShape<L>::M);
-  dim3 grid(blocks_for(T.count, TnShape<L>::M), p.batch);
-  k_restrict<L, S, true, MOV><<<grid, block, 0, s>>>(p, c, T, resc, ppar, cpar, R, pdu, omega_p,
-                                                      sig, ks_p);
+  const RstDesc J = rst_desc<L>(T);
+  dim3 block(32, RstTile<L>::NW);
+  dim3 grid((unsigned)J.tstart[T.nf], p.batch);
+  k_restrict_tile<L, S, true, MOV><<<grid, block, 0, s>>>(p, c, T, J, resc, ppar, cpar, R, pdu,
+                                                          omega_p, sig, ks_p);
 }
 
 template <class L>
