@@ -683,6 +683,7 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
   const int pn1 = pick(R.pn, t1), pn2 = pick(R.pn, t2);
   const float* h = R.hist + (long long)run * 3 * R.nv * R.K;
   const long long K = R.K, nv = R.nv;
+  const bool one_slot = w0 == 0.0f && w1 == 0.0f;  // uniform over the grid
   // stage: parent window x values, interpolated in time
   const int tid = (threadIdx.z * T::TJ + threadIdx.y) * T::TI + threadIdx.x;
 #pragma unroll 4
@@ -709,10 +710,14 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
       }
     }
     float val = 0.0f;
-    if (ok)
-      val = w0 * h[((long long)s_m1 * nv + vv) * K + idx] +
-            w1 * h[((long long)s_0 * nv + vv) * K + idx] +
-            w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+    if (ok) {
+      if (one_slot)  // the synchronous sub-step: t+1 only
+        val = w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+      else
+        val = w0 * h[((long long)s_m1 * nv + vv) * K + idx] +
+              w1 * h[((long long)s_0 * nv + vv) * K + idx] +
+              w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+    }
     sv[vv][pj][pi] = val;
   }
   __syncthreads();
@@ -809,6 +814,7 @@ __global__ void __launch_bounds__(InjSep<L>::NT)
   const int pn1 = pick(R.pn, t1), pn2 = pick(R.pn, t2);
   const float* h = R.hist + (long long)run * 3 * R.nv * R.K;
   const long long K = R.K, nv = R.nv;
+  const bool one_slot = w0 == 0.0f && w1 == 0.0f;  // uniform over the grid
   const int tid = threadIdx.y * T::TI + threadIdx.x;
   // stage (eq. TempInt)
 #pragma unroll(T::UNR)
@@ -832,10 +838,14 @@ __global__ void __launch_bounds__(InjSep<L>::NT)
       idx += (long long)rj * st2;
     }
     float val = 0.0f;
-    if (ok)
-      val = w0 * h[((long long)s_m1 * nv + vv) * K + idx] +
-            w1 * h[((long long)s_0 * nv + vv) * K + idx] +
-            w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+    if (ok) {
+      if (one_slot)  // the synchronous sub-step: t+1 only
+        val = w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+      else
+        val = w0 * h[((long long)s_m1 * nv + vv) * K + idx] +
+              w1 * h[((long long)s_0 * nv + vv) * K + idx] +
+              w2 * h[((long long)s_p1 * nv + vv) * K + idx];
+    }
     sv[vv][pj][pi] = val;
   }
   __syncthreads();
