@@ -56,6 +56,7 @@ extern "C" {
 #define LBM_ECUDA (-3)     /* a CUDA runtime call or launch failed */
 #define LBM_EUNSTABLE (-4) /* non-finite mass found by lbm_diag */
 #define LBM_ESTATE (-5)    /* call out of order (e.g. step before init) */
+#define LBM_ETIMEOUT (-6)  /* a bounded device-side wait ran out (lbm_set_fused) */
 
 /* Lattices (Sec. 3.1; 3D sets of the same Hermite construction). */
 #define LBM_D2Q9 0
@@ -189,6 +190,22 @@ int lbm_step(lbm_handle h, int n_coarse);
 
 /* Use (1, default) or bypass (0) CUDA graphs in lbm_step. */
 int lbm_set_graphs(lbm_handle h, int enable);
+
+/* Persistent fused step (mode 1; 0 = off, the default): from the second
+ * coarse step on, lbm_step(h, n) issues one cooperative kernel per 1024
+ * coarse steps that runs every level update, history capture, rebuild,
+ * restriction and probe of those steps in the scheduler's order, separated
+ * by grid barriers, instead of one kernel per operation.  Meant for small
+ * runs, whose per-operation kernels are dominated by launch and drain
+ * time.  Plain, regularized and recursive regularized collisions without
+ * sensors (LBM_EINVAL for the hybrid collision; while sensors are on, or
+ * while profiling, lbm_step uses the per-operation kernels).  Every
+ * barrier wait is bounded (about a second); if one runs out the kernel
+ * stops, the run's state is lost, and the next lbm_step or lbm_sync
+ * returns LBM_ETIMEOUT until lbm_set_fused is called again.  Mode 2 is a
+ * test of that path: its barriers wait for one block more than the launch
+ * has and give up after a few milliseconds.  Synchronises. */
+int lbm_set_fused(lbm_handle h, int mode);
 
 /* Macroscopic density and velocity of one level of one run, from the
  * post-collision state after the last step: rho host [N], u host [3][N]

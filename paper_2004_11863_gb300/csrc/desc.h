@@ -158,4 +158,49 @@ struct TnDesc {
   int boxed[3];
 };
 
+// Persistent fused step (kernels_fused.cuh): the recorded program, the
+// launch arguments and the host-side description of the tables it reads.
+constexpr int kFusedLevels = 4;
+struct FusedTables;  // device tables (kernels_fused.cuh)
+
+// One phase of a recorded coarse step.
+struct Phase {
+  int kind;     // 0 update, 1 capture, 2 rebuild, 3 restriction, 4 probe
+  int level;    // update / rebuild / probe: that level; capture / restriction: the parent
+  int par;      // update: its parity; capture: the parent's next update; rebuild: the
+                // child's next update; restriction: the parent's next update; probe: last
+  int cpar;     // restriction: the child's next update
+  int slot[3];  // rebuild: history slots of t-1, t, t+1; capture: [0] the receiving slot
+  float w[3];   // rebuild: temporal weights on those slots
+  float resc;   // rebuild (eq. rescff) / restriction (eq. rescfc)
+  float omega;  // update
+  int nobar;    // 1: the next phase touches nothing this one does; no grid barrier between
+};
+constexpr int kFusedMaxPhases = 192;  // six coarse steps' programs, cached in shared memory
+
+struct FusedArgs {
+  const FusedTables* tab;     // device
+  const Phase* prog;          // device: the six programs back to back
+  const int* prog_start;      // device [7]: program k is prog[prog_start[k] .. prog_start[k + 1])
+  int first_key, nsteps;      // key of the first coarse step (its index mod 6), steps to take
+  unsigned* bar;              // device [2]: arrival counter, generation
+  int* err;                   // device: error word of this launch
+  int* err_host;              // mapped host memory: the error word after the launch
+  long long spin_limit;       // bounded waits
+  int expect_extra;           // barrier expects this many blocks beyond the grid (0; tests > 0)
+};
+
+struct FusedHost {
+  LevelView v[kFusedLevels];
+  RingDesc ring[kFusedLevels];
+  BndDesc bnd[kFusedLevels];
+  TnDesc tn[kFusedLevels];
+  RefState refd;
+  int coll;
+  int probe_n, probe_cap;
+  const int* probe_ijk;
+  double* probe_rec;
+  unsigned long long* probe_counter;
+};
+
 }  // namespace mlbm

@@ -1,0 +1,54 @@
+// Host side of the persistent fused step for one lattice (included by the
+// three fused_<lattice>.cu translation units).
+#pragma once
+#include "kernels_fused.cuh"
+#include "ops_impl.cuh"
+
+namespace mlbm {
+
+template <class L>
+size_t fused_tab_bytes() {
+  return sizeof(FusedTables);
+}
+
+template <class L>
+cudaError_t fused_setup(const FusedHost& hst, void* d_tab) {
+  FusedTables t{};
+  for (int l = 0; l < kFusedLevels; ++l) {
+    t.v[l] = hst.v[l];
+    t.ring[l] = hst.ring[l];
+    t.bnd[l] = hst.bnd[l];
+    t.tn[l] = hst.tn[l];
+  }
+  t.ref = detail::make_ref_f<L>(hst.refd);
+  t.refd = hst.refd;
+  t.coll = hst.coll;
+  t.probe_n = hst.probe_n;
+  t.probe_cap = hst.probe_cap;
+  t.probe_ijk = hst.probe_ijk;
+  t.probe_rec = hst.probe_rec;
+  t.probe_counter = hst.probe_counter;
+  return cudaMemcpy(d_tab, &t, sizeof(t), cudaMemcpyHostToDevice);
+}
+
+template <class L>
+int fused_max_blocks(int storage) {
+  int per_sm = 0, dev = 0, sms = 0;
+  const void* k = storage == 0 ? (const void*)k_fused<L, float> : (const void*)k_fused<L, __half>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFusedThreads, 0) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms;
+}
+
+template <class L>
+cudaError_t fused_launch(const FusedArgs& A, int storage, int blocks, cudaStream_t s) {
+  void* args[] = {const_cast<FusedArgs*>(&A)};
+  const void* k = storage == 0 ? (const void*)k_fused<L, float> : (const void*)k_fused<L, __half>;
+  return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kFusedThreads), args, 0, s);
+}
+
+}  // namespace mlbm

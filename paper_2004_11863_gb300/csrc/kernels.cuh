@@ -543,11 +543,9 @@ __device__ __forceinline__ int ring_face(const long long* start, int nf, long lo
 // (drho, du, 0) of the parent's current state (laid out after an update of
 // parity `par`) into slots `s_new` and `s_also`.
 template <class L, class S>
-__global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new, int s_also,
-                          RefF ref) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int run = blockIdx.y;
-  if (k >= R.K) return;
+__device__ __forceinline__ void capture_item(const LevelView& p, const RingDesc& R, int par,
+                                             int mode, int s_new, int s_also, const RefF& ref,
+                                             long long k, int run) {
   const int fc = ring_face(R.start, R.nf, k);
   long long loc = k - R.start[fc];
   int P[3];
@@ -581,6 +579,14 @@ __global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new,
       hs[(long long)(4 + i) * R.K] = (mode == 0) ? f1[i] : 0.0f;
     });
   }
+}
+
+template <class L, class S>
+__global__ void k_capture(LevelView p, RingDesc R, int par, int mode, int s_new, int s_also,
+                          RefF ref) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= R.K) return;
+  capture_item<L, S>(p, R, par, mode, s_new, s_also, ref, k, blockIdx.y);
 }
 
 // ------------------------------------------------------------- K3: inject

@@ -166,6 +166,21 @@ struct lbm_ctx {
     }
     return event_pool[pool_used++];
   }
+  // persistent fused step (lbm_set_fused): the programs of six coarse steps
+  // (recorded from the scheduler with launch = false), their device copies,
+  // the tables they read, the grid barrier words and the error words
+  int fused = 0;                      // 0 off, 1 on, 2 test: barrier that cannot complete
+  bool fused_valid = false;           // programs and tables match the current set-up
+  std::vector<Phase>* recording = nullptr;
+  std::vector<Phase> prog[kPhases];
+  void* fused_tab = nullptr;
+  Phase* fused_prog = nullptr;
+  int* fused_start = nullptr;
+  unsigned* fused_bar = nullptr;
+  int* fused_err = nullptr;
+  int* fused_err_host = nullptr;      // mapped pinned host memory
+  int* fused_err_dev = nullptr;       // its device alias
+  int fused_blocks = 0;
   // probes
   int probe_level = -1, probe_n = 0, probe_cap = 0;
   long long probe_pending = 0;  // coarse steps recorded since the last read-out
@@ -226,6 +241,7 @@ Ops ops_for(int lattice) {
 }
 
 void drop_graphs(lbm_ctx* h) {
+  h->fused_valid = false;
   for (int k = 0; k < lbm_ctx::kPhases; ++k)
     if (h->exec[k]) {
       cudaGraphExecDestroy(h->exec[k]);
@@ -250,6 +266,17 @@ void release(lbm_ctx* h) {
   h->dfree(h->probe_rec);
   h->dfree(h->probe_counter);
   h->scratch_drop();
+  h->dfree(h->fused_tab);
+  h->dfree(h->fused_prog);
+  h->dfree(h->fused_start);
+  h->dfree(h->fused_bar);
+  h->dfree(h->fused_err);
+  h->fused_tab = h->fused_prog = nullptr;
+  h->fused_start = nullptr;
+  h->fused_bar = nullptr;
+  h->fused_err = nullptr;
+  if (h->fused_err_host) cudaFreeHost(h->fused_err_host);
+  h->fused_err_host = h->fused_err_dev = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int l = 0; l < LBM_MAX_LEVELS; ++l) {
     if (h->side[l]) cudaStreamDestroy(h->side[l]);
@@ -515,11 +542,16 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     const Level& p = h->lev[l - 1];
     const float resc = (float)(v.tau / (2.0 * p.tau));  // eq. rescff
     const int slots[3] = {(v.head + 1) % 3, (v.head + 2) % 3, v.head};  // t-1, t, t+1
+    if (h->recording)
+      h->recording->push_back(Phase{2, l, par, 0, {slots[0], slots[1], slots[2]},
+                                    {wt[0], wt[1], wt[2]}, resc, 0.0f});
     LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref, h->cur));
   }
   if (l + 1 < h->nlev) {
     Level& c = h->lev[l + 1];
     c.head = (c.head + 1) % 3;
+    if (h->recording)
+      h->recording->push_back(Phase{1, l, par, 0, {c.head, c.head, c.head}, {}, 0.0f, 0.0f});
     LAUNCH_K(1, l, h->ops.capture(v.view, c.ring, st, par, 0, c.head, c.head, ref, h->cur));
     int rc = advance(h, l + 1, v.nsteps == 0 ? kTimeLin : kTimeQuad, launch, nullptr);
     if (rc) return rc;
@@ -537,6 +569,11 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
       h->cur = h->side[l];
     }
     const float resc = (float)(2.0 * v.tau / c.tau);  // eq. rescfc
+    // (recorded for the fused step with no barrier after it: the child's
+    // second rebuild, next in the program, touches other cells -- the
+    // streams above run the two side by side)
+    if (h->recording)
+      h->recording->push_back(Phase{3, l, par, 1 - c.last, {}, {}, resc, 0.0f, 1});
     LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref, h->cur));
     if (fork) CK(cudaEventRecord(h->ev_restrict[l], h->side[l]));
     int rs = sensor_pass(h, l, par, launch, true);
@@ -544,6 +581,10 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     // (this level may itself be a second sub-step whose update must wait
     // for its parent's restriction)
     if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
+    // (recorded for the fused step after the child's second rebuild, with
+    // no barrier before the child's next phase: nothing there reads or
+    // writes this level's populations)
+    const Phase upd{0, l, par, 0, {}, {}, 0.0f, omega_of(v.tau), 1};
     LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
                                          v.k1_bx, v.k1_by, h->cur));
     if (fork) {
@@ -552,14 +593,17 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     }
     v.last = par;
     v.nsteps++;
+    const size_t at = h->recording ? h->recording->size() : 0;
     rc = advance(h, l + 1, kTimeDirect, launch, fork ? h->ev_restrict[l] : nullptr);
     if (rc) return rc;
+    if (h->recording) h->recording->insert(h->recording->begin() + at + 1, upd);
     if (fork) CK(cudaStreamWaitEvent(main, h->ev_join[l], 0));
     return LBM_OK;
   }
   int rs = sensor_pass(h, l, par, launch, true);
   if (rs) return rs;
   if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
+  if (h->recording) h->recording->push_back(Phase{0, l, par, 0, {}, {}, 0.0f, omega_of(v.tau)});
   LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
                                        v.k1_bx, v.k1_by, h->cur));
   v.last = par;
@@ -653,6 +697,11 @@ int advance_hrr(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wai
 int probe_launch(lbm_ctx* h, bool launch) {
   if (h->probe_n <= 0) return LBM_OK;
   const Level& v = h->lev[h->probe_level];
+  // (for the fused step: with two or more levels the next coarse step
+  // starts with a capture, which writes only the history)
+  if (h->recording)
+    h->recording->push_back(Phase{4, h->probe_level, v.last, 0, {}, {}, 0.0f, 0.0f,
+                                  h->nlev > 1 ? 1 : 0});
   LAUNCH_K(4, h->probe_level, h->ops.probe(v.view, h->cfg.storage, v.last, h->probe_ijk, h->probe_n, h->probe_rec,
                       h->probe_cap, h->probe_counter, h->ref, h->cur));
   return LBM_OK;
@@ -697,6 +746,7 @@ const char* lbm_strerror(int code) {
     case LBM_ECUDA: return g_errmsg[0] ? g_errmsg : "CUDA error";
     case LBM_EUNSTABLE: return "non-finite mass: the run is unstable";
     case LBM_ESTATE: return "call out of order (initialise every level and run first)";
+    case LBM_ETIMEOUT: return "a grid barrier wait of the fused step ran out; the run's state is lost";
     default: return "unknown error";
   }
 }
@@ -1031,6 +1081,156 @@ int lbm_set_graphs(lbm_handle h, int enable) {
   return LBM_OK;
 }
 
+namespace {
+
+// The fused step covers the plain, regularized and recursive regularized
+// collisions without sensors, outside the per-kernel profiling mode.
+bool fused_usable(const lbm_ctx* h) {
+  if (!h->fused || h->profiling || h->cfg.collision == LBM_HRR) return false;
+  for (int l = 0; l < h->nlev; ++l)
+    if (h->lev[l].sens_on) return false;
+  return true;
+}
+
+// Record the programs of the six coarse steps that follow the current state
+// (the scheduler with launch = false: host bookkeeping only, undone after),
+// upload them and the tables they read, and size the grid: one thread per
+// item of the largest phase, at most the co-resident grid.
+int fused_prepare(lbm_ctx* h) {
+  int head[LBM_MAX_LEVELS], last[LBM_MAX_LEVELS];
+  long long nsteps[LBM_MAX_LEVELS];
+  for (int l = 0; l < h->nlev; ++l) {
+    head[l] = h->lev[l].head;
+    last[l] = h->lev[l].last;
+    nsteps[l] = h->lev[l].nsteps;
+  }
+  int rc = LBM_OK;
+  for (int k = 0; k < lbm_ctx::kPhases; ++k) h->prog[k].clear();
+  for (int s = 0; s < lbm_ctx::kPhases && rc == LBM_OK; ++s) {
+    h->recording = &h->prog[(h->coarse_steps + s) % lbm_ctx::kPhases];
+    rc = coarse_step(h, false);
+  }
+  h->recording = nullptr;
+  for (int l = 0; l < h->nlev; ++l) {
+    h->lev[l].head = head[l];
+    h->lev[l].last = last[l];
+    h->lev[l].nsteps = nsteps[l];
+  }
+  if (rc) return rc;
+  size_t total = 0;
+  for (int k = 0; k < lbm_ctx::kPhases; ++k) total += h->prog[k].size();
+  if (total > (size_t)kFusedMaxPhases) return LBM_EINVAL;
+  std::vector<Phase> all;
+  int start[lbm_ctx::kPhases + 1];
+  start[0] = 0;
+  for (int k = 0; k < lbm_ctx::kPhases; ++k) {
+    all.insert(all.end(), h->prog[k].begin(), h->prog[k].end());
+    start[k + 1] = (int)all.size();
+  }
+  CK(cudaStreamSynchronize(h->stream));  // no fused launch still reads the old copies
+  h->dfree(h->fused_prog);
+  h->fused_prog = (Phase*)h->dalloc(sizeof(Phase) * all.size());
+  if (!h->fused_tab) h->fused_tab = h->dalloc(h->ops.fused_tab_bytes());
+  if (!h->fused_start) h->fused_start = (int*)h->dalloc(sizeof(start));
+  if (!h->fused_bar) h->fused_bar = (unsigned*)h->dalloc(2 * sizeof(unsigned));
+  if (!h->fused_err) h->fused_err = (int*)h->dalloc(sizeof(int));
+  if (!h->fused_prog || !h->fused_tab || !h->fused_start || !h->fused_bar || !h->fused_err)
+    return LBM_ENOMEM;
+  CK(cudaMemcpy(h->fused_prog, all.data(), sizeof(Phase) * all.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->fused_start, start, sizeof(start), cudaMemcpyHostToDevice));
+  FusedHost hst{};
+  long long items = 1;
+  for (int l = 0; l < h->nlev; ++l) {
+    const Level& v = h->lev[l];
+    hst.v[l] = v.view;
+    hst.ring[l] = v.ring;
+    hst.bnd[l] = v.bnd;
+    hst.tn[l] = v.tn;
+    items = std::max(items, v.n_nodes * h->batch);
+  }
+  hst.refd = h->ref;
+  hst.coll = h->cfg.collision;
+  hst.probe_n = h->probe_n;
+  hst.probe_cap = h->probe_cap;
+  hst.probe_ijk = h->probe_ijk;
+  hst.probe_rec = h->probe_rec;
+  hst.probe_counter = h->probe_counter;
+  CK(h->ops.fused_setup(hst, h->fused_tab));
+  const int maxb = h->ops.fused_max_blocks(h->cfg.storage);
+  if (maxb <= 0) {
+    snprintf(g_errmsg, sizeof(g_errmsg), "fused step: no co-resident grid");
+    return LBM_ECUDA;
+  }
+  h->fused_blocks = (int)std::min<long long>(maxb, (items + 255) / 256);
+  h->fused_valid = true;
+  return LBM_OK;
+}
+
+// n coarse steps in cooperative launches of at most 1024 steps each; the
+// host-side bookkeeping of every step follows as for graph replays.
+int fused_steps(lbm_ctx* h, int n) {
+  if (h->fused_err_host && *(volatile int*)h->fused_err_host) return LBM_ETIMEOUT;
+  if (!h->fused_valid) {
+    int rc = fused_prepare(h);
+    if (rc) return rc;
+  }
+  while (n > 0) {
+    const int chunk = std::min(n, 1024);
+    CK(cudaMemsetAsync(h->fused_bar, 0, 2 * sizeof(unsigned), h->stream));
+    CK(cudaMemsetAsync(h->fused_err, 0, sizeof(int), h->stream));
+    FusedArgs A{};
+    A.tab = (const FusedTables*)h->fused_tab;
+    A.prog = h->fused_prog;
+    A.prog_start = h->fused_start;
+    A.first_key = (int)(h->coarse_steps % lbm_ctx::kPhases);
+    A.nsteps = chunk;
+    A.bar = h->fused_bar;
+    A.err = h->fused_err;
+    A.err_host = h->fused_err_dev;
+    // about a second of waiting (each probe of the barrier word sleeps
+    // 128 ns and reads global memory); the barrier test needs milliseconds
+    A.spin_limit = h->fused == 2 ? (1LL << 12) : (1LL << 21);
+    A.expect_extra = h->fused == 2 ? 1 : 0;
+    CK(h->ops.fused(A, h->cfg.storage, h->fused_blocks, h->stream));
+    ++h->launches;
+    for (int s = 0; s < chunk; ++s) {
+      int rc = coarse_step(h, false);
+      if (rc) return rc;
+      ++h->coarse_steps;
+      if (h->probe_n > 0) ++h->probe_pending;
+    }
+    n -= chunk;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_set_fused(lbm_handle h, int mode) {
+  if (!h || mode < 0 || mode > 2) return LBM_EINVAL;
+  if (mode != 0 && h->cfg.collision == LBM_HRR) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  if (mode != 0 && !h->fused_err_host) {
+    int* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return LBM_ENOMEM;
+    }
+    int* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(p);
+      return LBM_ECUDA;
+    }
+    h->fused_err_host = p;
+    h->fused_err_dev = d;
+  }
+  if (h->fused_err_host) *(volatile int*)h->fused_err_host = 0;
+  h->fused = mode;
+  h->fused_valid = false;
+  return LBM_OK;
+}
+
 int lbm_step(lbm_handle h, int n_coarse) {
   if (!h || n_coarse < 0) return LBM_EINVAL;
   if (!h->ready) return LBM_ESTATE;
@@ -1040,6 +1240,9 @@ int lbm_step(lbm_handle h, int n_coarse) {
     if (rc) return rc;
   }
   for (int s = 0; s < n_coarse; ++s) {
+    // the first coarse step (first sub-steps with one history slot) stays
+    // on the per-phase kernels; the fused programs start after it
+    if (h->coarse_steps > 0 && fused_usable(h)) return fused_steps(h, n_coarse - s);
     if (h->coarse_steps == 0 || !h->use_graphs || h->profiling) {
       h->cur = h->stream;
       int rc = coarse_step(h, true);
@@ -1392,6 +1595,7 @@ int lbm_diag(lbm_handle h, int run, double* mass, double* mom) {
 int lbm_sync(lbm_handle h) {
   if (!h) return LBM_EINVAL;
   CK(cudaStreamSynchronize(h->stream));
+  if (h->fused_err_host && *(volatile int*)h->fused_err_host) return LBM_ETIMEOUT;
   return LBM_OK;
 }
 

@@ -67,7 +67,24 @@ struct Ops {
   cudaError_t (*probe)(const LevelView& v, int storage, int last, const int* ijk, int n,
                        double* rec, int cap, unsigned long long* counter, const RefState& ref,
                        cudaStream_t s);
+  // Persistent fused step (kernels_fused.cuh): bytes of the device tables;
+  // fill them from the host description (synchronous copy); the largest
+  // co-resident grid; one cooperative launch of `blocks` blocks.
+  size_t (*fused_tab_bytes)();
+  cudaError_t (*fused_setup)(const FusedHost& hst, void* d_tab);
+  int (*fused_max_blocks)(int storage);
+  cudaError_t (*fused)(const FusedArgs& A, int storage, int blocks, cudaStream_t s);
 };
+
+// (instantiated per lattice in fused_d2q9.cu, fused_d3q19.cu, fused_d3q27.cu)
+template <class L>
+size_t fused_tab_bytes();
+template <class L>
+cudaError_t fused_setup(const FusedHost& hst, void* d_tab);
+template <class L>
+int fused_max_blocks(int storage);
+template <class L>
+cudaError_t fused_launch(const FusedArgs& A, int storage, int blocks, cudaStream_t s);
 
 struct D2Q9;
 struct D3Q19;

@@ -474,6 +474,10 @@ Ops make_ops() {
   o.diag_partial = detail::diag_partial<L>;
   o.noise_partial = detail::noise_partial<L>;
   o.probe = detail::probe<L>;
+  o.fused_tab_bytes = fused_tab_bytes<L>;
+  o.fused_setup = fused_setup<L>;
+  o.fused_max_blocks = fused_max_blocks<L>;
+  o.fused = fused_launch<L>;
   return o;
 }
 

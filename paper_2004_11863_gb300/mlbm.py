@@ -21,7 +21,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmlbm.so")
 
 LBM_OK = 0
-ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ESTATE"}
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "ESTATE",
+          -6: "ETIMEOUT"}
 STORAGE = {"fp32": 0, "fp16": 1}
 MAX_LEVELS = 4
 
@@ -83,6 +84,7 @@ def lib():
     L.lbm_init.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
     L.lbm_step.argtypes = [P, ctypes.c_int]
     L.lbm_set_graphs.argtypes = [P, ctypes.c_int]
+    L.lbm_set_fused.argtypes = [P, ctypes.c_int]
     L.lbm_macros.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
     L.lbm_macros_device.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     L.lbm_populations.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
@@ -280,6 +282,13 @@ class Lbm:
 
     def set_graphs(self, enable: bool):
         _check(lib().lbm_set_graphs(self._h, int(bool(enable))), "lbm_set_graphs")
+
+    def set_fused(self, mode=1):
+        """lbm_set_fused: 1 runs every coarse step after the first as one
+        persistent cooperative kernel; 0 (default) the per-operation
+        kernels; 2 tests the bounded barrier wait (the next sync raises
+        LbmError with code -6)."""
+        _check(lib().lbm_set_fused(self._h, int(mode)), "lbm_set_fused")
 
     def macros(self, level, run=0, out=None):
         """lbm_macros: (rho [N], u [3, N]) float64.  out: optional

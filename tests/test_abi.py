@@ -84,4 +84,5 @@ def test_null_arguments(lib):
     assert lib.lbm_set_block_shape(None, 0, 32, 4) == -1
     assert lib.lbm_sensors(None, 0, 0, None, None, None, None) == -1
     assert lib.lbm_probe_async(None, None, 0, None) == -1
+    assert lib.lbm_set_fused(None, 1) == -1
     lib.lbm_destroy(None)
