@@ -481,6 +481,35 @@ def main():
                     "with the library's defaults",
         }
 
+    # ---------------- persistent fused step vs graph replay on small runs --
+    # (lbm_set_fused: one cooperative kernel per lbm_step call; the default
+    # path replays one CUDA graph per coarse step)
+    fused_cmp = None
+    if args.serve > 0:
+        fused_cmp = {}
+        small = {
+            "d2q9_64": W.Case("s2d", "D2Q9", "RR", 0.52, (64, 64, 1), [((16, 16, 0), (48, 48, 1))],
+                              dict(kind="pulse", center=(21.0, 32.0, 0.0), radius=3.0,
+                                   amplitude=1e-3), 200),
+            "d3q19_32": W.Case("s3d", "D3Q19", "RR", 0.52, (32, 32, 32),
+                               [((8, 8, 8), (24, 24, 24))],
+                               dict(kind="pulse", center=(11.0, 16.0, 16.0), radius=3.0,
+                                    amplitude=1e-3), 200),
+        }
+        for key, sc in small.items():
+            row = {}
+            for mode, label in ((0, "graphs_us_per_coarse_step"), (1, "fused_us_per_coarse_step")):
+                g = mlbm.Lbm.from_case(sc)
+                g.set_fused(mode)
+                g.step(8)
+                g.sync()
+                t0 = time.perf_counter()
+                g.step(sc.steps)
+                g.sync()
+                row[label] = round((time.perf_counter() - t0) / sc.steps * 1e6, 1)
+                g.close()
+            fused_cmp[key] = row
+
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline(case)
@@ -512,6 +541,7 @@ def main():
         "e2e": e2e,
         "variants": variants,
         "serving": serving,
+        "fused_step_small_runs": fused_cmp,
         "cpu_baseline": cpu,
         "stable": bool(stable),
     }
