@@ -176,7 +176,7 @@ struct Phase {
   float omega;  // update
   int nobar;    // 1: the next phase touches nothing this one does; no grid barrier between
 };
-constexpr int kFusedMaxPhases = 192;  // six coarse steps' programs, cached in shared memory
+constexpr int kFusedMaxPhases = 264;  // six coarse steps of four levels, cached in shared memory
 
 struct FusedArgs {
   const FusedTables* tab;     // device

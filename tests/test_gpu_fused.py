@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_2004_11863_gb300 import workloads as W
+from tests.test_gpu_parity import FOUR_LEVELS
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +49,7 @@ CASES = [
     ("d3q19_2lev", lambda: W.small_3d("D3Q19", "RR", nlevels=2, steps=6)),
     ("d3q27_3lev", lambda: W.small_3d("D3Q27", "RR", nlevels=3, steps=4)),
     ("d3q19_slab", lambda: W.slab_small_3d("D3Q19", "RR", steps=6)),
+    ("four_levels_2d", lambda: FOUR_LEVELS),
     ("d3q27_tube", lambda: W.Case("tube3d", "D3Q27", "RR", 0.52, (29, 16, 17),
                                   [((0, 4, 4), (29, 12, 13))],
                                   dict(kind="pulse", center=(27.0, 6.0, 8.0), radius=3.0,

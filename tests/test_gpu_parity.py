@@ -138,6 +138,23 @@ def test_three_level_2d(M):
     compare(g, o, 3)
 
 
+FOUR_LEVELS = W.Case("nest4", "D2Q9", "RR", 0.51, (40, 40, 1),
+                     [((10, 10, 0), (30, 30, 1))] * 3,
+                     dict(kind="pulse", center=(19.0, 21.0, 0.0), radius=3.0, amplitude=1e-3,
+                          u0=(0.05 * W.CS, 0.0, 0.0)), 6)
+
+
+def test_four_levels_2d(M):
+    """The deepest nesting the library allows (four levels, 8 finest
+    sub-steps per coarse step)."""
+    case = FOUR_LEVELS
+    g = M.Lbm.from_case(case)
+    o = oracle.Run.from_case(case)
+    g.step(case.steps)
+    o.step(case.steps)
+    compare(g, o, 4)
+
+
 def test_odd_and_even_step_counts(M):
     """AA parity: 1, 2 and 3 coarse steps all match (each level ends on
     either parity)."""
