@@ -269,9 +269,11 @@ int lbm_diag(lbm_handle h, int run, double* mass, double* mom);
  * the library (held by every GPU that loads the library until the process
  * exits).  Limit: every level of the run must have at most 16,777,216 nodes
  * (2^24); a run with a larger level is rejected with LBM_EINVAL before any
- * device work.  The first call on a device looks the array's address up
- * once for that device (so make that first call with the handle's device
- * current and before any stream capture).  All calls share the one array:
+ * device work.  Every call must be made with the handle's device current
+ * (the device that was current at lbm_create); otherwise it returns
+ * LBM_EINVAL before any device work.  The first call on a device looks the
+ * array's address up once for that device, so make that first call before
+ * any stream capture.  All calls share the one array:
  * calls whose device work overlaps in time (different streams, or several
  * handles at once) race and must be serialised by the caller; nothing in the
  * array needs clearing, because every call writes each value before reading

@@ -127,6 +127,7 @@ struct lbm_ctx {
   RefState ref{};  // reference state of the shifted storage
   int q = 0, D = 0, nlev = 0, batch = 1;
   Ops ops{};
+  int device = -1;  // the device current at lbm_create (the stream's device)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cur = nullptr;
@@ -821,6 +822,10 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
     }
   }
   for (int l = 1; l < h->nlev; ++l) build_interface(h, l);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return LBM_ECUDA;
+  }
   // device memory
   for (int l = 0; l < h->nlev; ++l) {
     Level& v = h->lev[l];
@@ -1187,8 +1192,9 @@ int fused_steps(lbm_ctx* h, int n) {
     A.bar = h->fused_bar;
     A.err = h->fused_err;
     A.err_host = h->fused_err_dev;
-    // about a second of waiting (each probe of the barrier word sleeps
-    // 128 ns and reads global memory); the barrier test needs milliseconds
+    // a bounded wait: 2^21 probes of the barrier word, the first 256 without
+    // sleeping and then 64 ns of __nanosleep each, about 0.13 s plus the
+    // read latency of every probe; the barrier test needs milliseconds
     A.spin_limit = h->fused == 2 ? (1LL << 12) : (1LL << 21);
     A.expect_extra = h->fused == 2 ? 1 : 0;
     CK(h->ops.fused(A, h->cfg.storage, h->fused_blocks, h->stream));
@@ -1671,11 +1677,9 @@ __global__ void k_diag_final(const double* partial, int nblocks, double* out) {
 std::mutex g_scratch_mu;
 void* g_scratch_ptr[64] = {};
 
-// Address of the scratch array on the current device, looked up once per
-// device.
-int scratch_on_current_device(double** out) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+// Address of the scratch array on device `dev` (which must be current),
+// looked up once per device.
+int scratch_on_device(int dev, double** out) {
   if (dev < 0 || dev >= 64) return LBM_EINVAL;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
@@ -1694,8 +1698,12 @@ extern "C" int lbm_diag_noalloc(lbm_handle h, int run, double* mass, double* mom
   for (int l = 0; l < h->nlev; ++l)
     if (h->lev[l].n_nodes > kNoAllocMaxNodes) return LBM_EINVAL;  // beyond the fixed scratch
   if (!h->ready) return LBM_ESTATE;
+  // the scratch address is per device: the handle's device must be current
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != h->device) return LBM_EINVAL;
   double* scratch = nullptr;
-  int rc = scratch_on_current_device(&scratch);
+  int rc = scratch_on_device(dev, &scratch);
   if (rc) return rc;
   double* partial = scratch;
   double* result = scratch + 4 * (long long)kNoAllocMaxBlocks;
