@@ -259,25 +259,35 @@ struct StripAddr {
   }
 };
 
+// Face buffer of a level whose x axis is bounded by its box: the rebuilt
+// pre-collision populations of the nodes on the two faces normal to x
+// (x = 0: side 0, x = n[0] - 1: side 1), written there by the coarse ->
+// fine rebuild instead of into the level's planes.  On those faces x is
+// the fastest axis of the planes, so each rebuilt population would land in
+// its own 32-byte sector; in the face buffer a face is a plane of its own
+// (y fastest), written and read in whole sectors.  Element of run r,
+// side s, direction i, face node (y, z):
+//   ((((r / es) * 2 + s) * q + i) * F + z * n[1] + y) * es + r % es,
+// F = n[1] * n[2].  The level update reads a face node's populations from
+// here; a warp holds such a node only if it covers x = 0 or x = n[0] - 1,
+// and only those warps take the selecting loads (a warp-uniform branch).
+__device__ __forceinline__ bool warp_has_xface(const LevelView& v, const void* xf) {
+  const int xw = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  return xf != nullptr && (xw == 0 || (xw <= v.n[0] - 1 && v.n[0] - 1 < xw + 32));
+}
+
 // One thread updates NPT nodes (x, y0 .. y0+NPT-1, z); a warp covers 32
 // consecutive x of NPT rows.  All loads of the thread's nodes are issued
 // before the first collision.  The block shape (blockDim.x a multiple of 32,
 // blockDim.x * blockDim.y <= 128) is chosen at run time (lbm_autotune); it
-// changes which nodes share a block, not any node's arithmetic.
-template <class L, int COLL, class S, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
-                                           : (PAR == 0 ? K1Tune<L, S>::MINB_EVEN
-                                                       : K1Tune<L, S>::MINB))
-    k_stream_collide(LevelView v, float omega, RefF R) {
+// changes which nodes share a block, not any node's arithmetic.  FACE: the
+// warp holds a node of a face normal to x, whose populations come from the
+// face buffer xf.
+template <class L, int COLL, class S, int PAR, bool MOV, bool FACE>
+__device__ __forceinline__ void stream_collide_body(const LevelView& v, float omega,
+                                                    const RefF& R, const S* __restrict__ xf,
+                                                    int x, int y0, int z, int run) {
   constexpr int NPT = K1Tune<L, S>::NPT;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * NPT;
-  int z = blockIdx.z, run = 0;
-  if (v.batch > 1) {
-    run = z / v.n[2];
-    z -= run * v.n[2];
-  }
-  if (x >= v.n[0] || y0 >= v.n[1]) return;
   S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
   StripAddr<NPT> a;
   const int off = (int)v.off;
@@ -300,6 +310,15 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
     if (v.per[1]) yy = wrapi(yy, v.n[1]);
     a.yo[r] = yy * v.SX;
   }
+  // face buffer of this lane's nodes (FACE warps only)
+  bool fx = false;
+  const S* xb = nullptr;
+  long long F = 0;
+  if constexpr (FACE) {
+    fx = x == 0 || x == v.n[0] - 1;
+    F = (long long)v.n[1] * v.n[2];
+    xb = xf + ((long long)run * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1] + y0;
+  }
   bool ok[NPT];
   float g[NPT][L::Q];
 #pragma unroll
@@ -308,6 +327,12 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
     if (ok[k]) {
       sfor<L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
+        if constexpr (FACE) {
+          if (fx) {
+            g[k][i] = Store<S>::ld(xb + i * F + k);
+            return;
+          }
+        }
         if constexpr (PAR == 0)
           g[k][i] = Store<S>::ld(f + (long long)i * v.plane + a.at(k, 0, 0, 0));
         else
@@ -328,6 +353,26 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
                      val);
     });
   }
+}
+
+template <class L, int COLL, class S, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
+                                           : (PAR == 0 ? K1Tune<L, S>::MINB_EVEN
+                                                       : K1Tune<L, S>::MINB))
+    k_stream_collide(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
+  constexpr int NPT = K1Tune<L, S>::NPT;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * NPT;
+  int z = blockIdx.z, run = 0;
+  if (v.batch > 1) {
+    run = z / v.n[2];
+    z -= run * v.n[2];
+  }
+  if (x >= v.n[0] || y0 >= v.n[1]) return;
+  if (warp_has_xface(v, xf))
+    stream_collide_body<L, COLL, S, PAR, MOV, true>(v, omega, R, xf, x, y0, z, run);
+  else
+    stream_collide_body<L, COLL, S, PAR, MOV, false>(v, omega, R, xf, x, y0, z, run);
 }
 
 // Level update, two nodes per thread in one two-lane collision: the nodes
@@ -399,30 +444,39 @@ struct K1X2Tune<D3Q27> {
   static constexpr int MINB_H = K1X2H_MINB_D3Q27;
 };
 
-template <class L, class S, int COLL, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
-                                                                      : K1X2Tune<L>::MINB_H)
-    k_stream_collide_x2(LevelView v, float omega, RefF R) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
-  int z = blockIdx.z, run = 0;
-  if (v.batch > 1) {
-    run = z / v.n[2];
-    z -= run * v.n[2];
-  }
-  if (x >= v.n[0]) return;
-  const bool ok0 = y0 < v.n[1] && !inactive(v, x, y0, z);
-  const bool ok1 = y0 + 1 < v.n[1] && !inactive(v, x, y0 + 1, z);
-  if (!ok0 && !ok1) return;
+template <class L, class S, int COLL, int PAR, bool MOV, bool FACE>
+__device__ __forceinline__ void stream_collide_x2_body(const LevelView& v, float omega,
+                                                       const RefF& R, const S* __restrict__ xf,
+                                                       int x, int y0, int z, int run, bool ok0,
+                                                       bool ok1) {
   S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
   // each lane's node; an idle lane reads its partner's
   const NodeAddr a0 = node_addr<L>(v, x, ok0 ? y0 : y0 + 1, z);
   const NodeAddr a1 = node_addr<L>(v, x, ok1 ? y0 + 1 : y0, z);
+  // face buffer of this lane's nodes (FACE warps only)
+  bool fx = false;
+  const S* xb0 = nullptr;
+  const S* xb1 = nullptr;
+  long long F = 0;
+  if constexpr (FACE) {
+    fx = x == 0 || x == v.n[0] - 1;
+    F = (long long)v.n[1] * v.n[2];
+    const S* xb = xf + ((long long)run * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1];
+    xb0 = xb + (ok0 ? y0 : y0 + 1);
+    xb1 = xb + (ok1 ? y0 + 1 : y0);
+  }
   // element offsets are formed whole before indexing (f[i * plane + at]):
   // per-direction base pointers would cost 64-bit registers per direction
   F2 g[L::Q];
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
+    if constexpr (FACE) {
+      if (fx) {
+        g[i].v.x = Store<S>::ld(xb0 + i * F);
+        g[i].v.y = Store<S>::ld(xb1 + i * F);
+        return;
+      }
+    }
     if constexpr (PAR == 0) {
       g[i].v.x = Store<S>::ld(&f[(long long)i * v.plane + a0.at(0, 0, 0)]);
       g[i].v.y = Store<S>::ld(&f[(long long)i * v.plane + a1.at(0, 0, 0)]);
@@ -447,6 +501,28 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<
                      val.v.y);
     }
   });
+}
+
+template <class L, class S, int COLL, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
+                                                                      : K1X2Tune<L>::MINB_H)
+    k_stream_collide_x2(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
+  int z = blockIdx.z, run = 0;
+  if (v.batch > 1) {
+    run = z / v.n[2];
+    z -= run * v.n[2];
+  }
+  if (x >= v.n[0]) return;
+  const bool ok0 = y0 < v.n[1] && !inactive(v, x, y0, z);
+  const bool ok1 = y0 + 1 < v.n[1] && !inactive(v, x, y0 + 1, z);
+  if (!ok0 && !ok1) return;
+  if (warp_has_xface(v, xf))
+    stream_collide_x2_body<L, S, COLL, PAR, MOV, true>(v, omega, R, xf, x, y0, z, run, ok0, ok1);
+  else
+    stream_collide_x2_body<L, S, COLL, PAR, MOV, false>(v, omega, R, xf, x, y0, z, run, ok0,
+                                                        ok1);
 }
 
 // Level update of binary16 storage with runs interleaved in pairs (es = 2):
@@ -480,26 +556,35 @@ struct K1PairTune<D3Q27> {
   static constexpr int MINB = K1P_MINB_D3Q27;
 };
 
-template <class L, int COLL, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
-    k_stream_collide_pair(LevelView v, float omega, RefF R) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int npairs = (v.batch + 1) / 2;
-  int z = blockIdx.z, pair = 0;
-  if (npairs > 1) {
-    pair = z / v.n[2];
-    z -= pair * v.n[2];
-  }
-  if (x >= v.n[0] || y >= v.n[1] || inactive(v, x, y, z)) return;
+template <class L, int COLL, int PAR, bool MOV, bool FACE>
+__device__ __forceinline__ void stream_collide_pair_body(const LevelView& v, float omega,
+                                                         const RefF& R,
+                                                         const __half* __restrict__ xf, int x,
+                                                         int y, int z, int pair) {
   // half2 units: a plane is plane / 2 of them, node e sits at e
   __half2* f = reinterpret_cast<__half2*>(static_cast<__half*>(v.f) + pair * v.run_stride);
   const long long ph = v.plane / 2;
   const NodeAddr a = node_addr<L>(v, x, y, z);
+  bool fx = false;
+  const __half2* xb = nullptr;
+  long long F = 0;
+  if constexpr (FACE) {
+    fx = x == 0 || x == v.n[0] - 1;
+    F = (long long)v.n[1] * v.n[2];
+    xb = reinterpret_cast<const __half2*>(xf) + ((long long)pair * 2 + (x != 0)) * L::Q * F +
+         (long long)z * v.n[1] + y;
+  }
   F2 g[L::Q];  // lane x: run 2p, lane y: run 2p+1
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     __half2 h;
+    if constexpr (FACE) {
+      if (fx) {
+        h = xb[i * F];
+        g[i].v = __half22float2(h);
+        return;
+      }
+    }
     if constexpr (PAR == 0)
       h = f[i * ph + a.at(0, 0, 0)];
     else
@@ -514,6 +599,24 @@ __global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
     else
       f[i * ph + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))] = h;
   });
+}
+
+template <class L, int COLL, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
+    k_stream_collide_pair(LevelView v, float omega, RefF R, const __half* __restrict__ xf) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int npairs = (v.batch + 1) / 2;
+  int z = blockIdx.z, pair = 0;
+  if (npairs > 1) {
+    pair = z / v.n[2];
+    z -= pair * v.n[2];
+  }
+  if (x >= v.n[0] || y >= v.n[1] || inactive(v, x, y, z)) return;
+  if (warp_has_xface(v, xf))
+    stream_collide_pair_body<L, COLL, PAR, MOV, true>(v, omega, R, xf, x, y, z, pair);
+  else
+    stream_collide_pair_body<L, COLL, PAR, MOV, false>(v, omega, R, xf, x, y, z, pair);
 }
 
 // (drho, du, f^(1)) of a population set (deviations from the reference).
@@ -637,11 +740,13 @@ __device__ __forceinline__ void store_pre_i(S* f, long long plane, const NodeAdd
 // Rebuild f = f0(rho, u) + resc f^(1) (eq. rescff) of child node (x, y, z)
 // from its interpolated values val(j) = (drho, du, f^(1)) and store, from
 // thread group grp of G, every G-th direction where the child's update of
-// parity par reads it.
+// parity par reads it -- or, for a node on a face normal to x when the
+// level has a face buffer (xs = its side, 0 or 1; -1 otherwise), into the
+// face buffer xf (its layout: see warp_has_xface).
 template <class L, class S, int G, class V>
 __device__ __forceinline__ void inject_rebuild(const LevelView& c, int run, int x, int y, int z,
                                                int par, float resc, const RefF& ref, int grp,
-                                               V val) {
+                                               V val, S* xf, int xs) {
   const float drho = val(0), dux = val(1), duy = val(2);
   const float duz = (L::D == 3) ? val(3) : 0.0f;
   const float Ux = ref.Ux, Uy = ref.Uy, Uz = (L::D == 3) ? ref.Uz : 0.0f;
@@ -652,12 +757,20 @@ __device__ __forceinline__ void inject_rebuild(const LevelView& c, int run, int 
   const float rho = ref.rho0 + drho;
   S* fb = run_ptr<S>(c, run);
   const NodeAddr ad = node_addr<L>(c, x, y, z);
+  const long long F = (long long)c.n[1] * c.n[2];
+  S* xb = nullptr;
+  if (xs >= 0)
+    xb = xf + ((((long long)(run / c.es) * 2 + xs) * L::Q * F + (long long)z * c.n[1] + y) * c.es +
+               run % c.es);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (i % G == grp) {
       const float g = eq_i<L, i, true>(drho, rho, dux, duy, duz, dusq, dA, ref) +
                       resc * val(4 + i);
-      store_pre_i<L, S, i>(fb, c.plane, ad, par, c.es, g);
+      if (xs >= 0)
+        Store<S>::st(xb + (long long)i * F * c.es, g);
+      else
+        store_pre_i<L, S, i>(fb, c.plane, ad, par, c.es, g);
     }
   });
 }
@@ -665,7 +778,7 @@ __device__ __forceinline__ void inject_rebuild(const LevelView& c, int run, int 
 template <class L, class S>
 __global__ void __launch_bounds__(InjTile<L>::NT)
     k_inject(LevelView c, InjDesc J, RingDesc R, float w0, float w1, float w2, int s_m1,
-             int s_0, int s_p1, float resc, int par, RefF ref) {
+             int s_0, int s_p1, float resc, int par, RefF ref, S* xf) {
   using T = InjTile<L>;
   constexpr bool SPLIT = T::G > 1;  // a node's values shared through shared memory
   __shared__ float sv[T::NV][T::WJ][T::WI];
@@ -772,7 +885,8 @@ __global__ void __launch_bounds__(InjTile<L>::NT)
     else
       return own[j];
   };
-  inject_rebuild<L, S, T::G>(c, run, Xn[0], Xn[1], Xn[2], par, resc, ref, tz, val);
+  inject_rebuild<L, S, T::G>(c, run, Xn[0], Xn[1], Xn[2], par, resc, ref, tz, val, xf,
+                             (xf != nullptr && a == 0) ? J.side[f] : -1);
 }
 
 // 3D rebuild with the tensor-product stencil of eq. spaceInt applied one
@@ -798,7 +912,7 @@ template <class L, class S>
 __global__ void __launch_bounds__(InjSep<L>::NT)
     k_inject_sep(LevelView c, const __grid_constant__ InjDesc J,
                  const __grid_constant__ RingDesc R, float w0, float w1, float w2, int s_m1,
-                 int s_0, int s_p1, float resc, int par, RefF ref) {
+                 int s_0, int s_p1, float resc, int par, RefF ref, S* xf) {
   static_assert(L::D == 3, "k_inject_sep is the 3D rebuild");
   using T = InjSep<L>;
   __shared__ float sv[T::NV][T::WJ][T::WI];  // parent window, interpolated in time
@@ -893,7 +1007,8 @@ __global__ void __launch_bounds__(InjSep<L>::NT)
     for (int j = 0; j < T::NV; ++j) own[j] = ta[j][b][tx];
   }
   inject_rebuild<L, S, 1>(c, run, Xn0, Xn1, Xn2, par, resc, ref, 0,
-                          [&](int j) { return own[j]; });
+                          [&](int j) { return own[j]; }, xf,
+                          (xf != nullptr && a == 0) ? J.side[f] : -1);
 }
 
 // Strain rate S = (grad u + grad u^T) / 2 by second-order central

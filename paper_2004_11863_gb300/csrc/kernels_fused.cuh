@@ -197,7 +197,7 @@ __device__ __forceinline__ void fused_inject(const LevelView& c, const BndDesc& 
     }
   }
   inject_rebuild<L, S, 1>(c, run, X0, X1, X2, ph.par, ph.resc, ref, 0,
-                          [&](int j) { return val[j]; });
+                          [&](int j) { return val[j]; }, static_cast<S*>(nullptr), -1);
 }
 
 // Restriction of TN node item t (run-major over the TN nodes of the child

@@ -70,6 +70,10 @@ struct Level {
   // (l >= 1) the parent strain-rate history [run][3][6][K]
   void* du_mem = nullptr;
   void* sh_mem = nullptr;
+  // (l >= 1, x bounded by the box, not the hybrid collision) face buffer of
+  // the nodes on the two faces normal to x: the rebuild writes their
+  // populations there and the level update reads them from there
+  void* xf_mem = nullptr;
   // block shape of the level update (lbm_autotune)
   int k1_bx = 32, k1_by = 4;
   // non-hydrodynamic mode sensors (lbm_sensors_enable)
@@ -260,6 +264,8 @@ void release(lbm_ctx* h) {
     h->dfree(h->lev[l].du_mem);
     h->dfree(h->lev[l].sh_mem);
     h->dfree(h->lev[l].sens_mem);
+    h->dfree(h->lev[l].xf_mem);
+    h->lev[l].xf_mem = nullptr;
     h->lev[l].mem = h->lev[l].hist_mem = h->lev[l].du_mem = h->lev[l].sh_mem = nullptr;
     h->lev[l].sens_mem = nullptr;
   }
@@ -493,6 +499,26 @@ size_t hrr_sh_bytes(const lbm_ctx* h, int l) {
   return sizeof(float) * 3 * 6 * (size_t)h->lev[l].ring.K * h->batch;
 }
 
+// Device bytes of level l's face buffer (faces normal to a bounded x axis;
+// the hybrid collision, whose velocity pass reads the rebuilt nodes from the
+// planes, has none): two faces of n[1] n[2] nodes, q populations, every run
+// (binary16 run pairs: the batch rounded up to whole pairs).
+size_t xf_bytes(const lbm_ctx* h, int l) {
+  const Level& v = h->lev[l];
+  if (l < 1 || !v.boxed[0] || h->cfg.collision == LBM_HRR) return 0;
+  const size_t es = v.view.es > 0 ? (size_t)v.view.es : 1;
+  const size_t runs = (h->batch + es - 1) / es * es;
+  const size_t s = h->cfg.storage == LBM_FP16_SHIFTED ? 2 : 4;
+  return s * runs * 2 * (size_t)h->q * (size_t)v.n[1] * (size_t)v.n[2];
+}
+
+// The face buffer level l's rebuild and update use now: none while the
+// level's sensors are on (they read the rebuilt nodes from the planes).
+void* xf_of(const lbm_ctx* h, int l) {
+  const Level& v = h->lev[l];
+  return v.sens_on ? nullptr : v.xf_mem;
+}
+
 const float kTimeQuad[3] = {-1.0f / 8.0f, 3.0f / 4.0f, 3.0f / 8.0f};  // eq. TempInt
 const float kTimeLin[3] = {0.0f, 0.5f, 0.5f};   // first step: no t-1 yet
 const float kTimeDirect[3] = {0.0f, 0.0f, 1.0f};  // synchronous sub-step
@@ -546,7 +572,8 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     if (h->recording)
       h->recording->push_back(Phase{2, l, par, 0, {slots[0], slots[1], slots[2]},
                                     {wt[0], wt[1], wt[2]}, resc, 0.0f});
-    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref, h->cur));
+    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref,
+                                 xf_of(h, l), h->cur));
   }
   if (l + 1 < h->nlev) {
     Level& c = h->lev[l + 1];
@@ -587,7 +614,7 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     // writes this level's populations)
     const Phase upd{0, l, par, 0, {}, {}, 0.0f, omega_of(v.tau), 1};
     LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
-                                         v.k1_bx, v.k1_by, h->cur));
+                                         v.k1_bx, v.k1_by, xf_of(h, l), h->cur));
     if (fork) {
       CK(cudaEventRecord(h->ev_join[l], h->side[l]));
       h->cur = main;
@@ -606,7 +633,7 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
   if (launch && wait_before_update) CK(cudaStreamWaitEvent(h->cur, wait_before_update, 0));
   if (h->recording) h->recording->push_back(Phase{0, l, par, 0, {}, {}, 0.0f, omega_of(v.tau)});
   LAUNCH_K(0, l, h->ops.stream_collide(v.view, h->cfg.collision, st, par, omega_of(v.tau), ref,
-                                       v.k1_bx, v.k1_by, h->cur));
+                                       v.k1_bx, v.k1_by, xf_of(h, l), h->cur));
   v.last = par;
   v.nsteps++;
   return LBM_OK;
@@ -639,7 +666,8 @@ int advance_hrr(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wai
     slots[0] = (v.head + 1) % 3;
     slots[1] = (v.head + 2) % 3;
     slots[2] = v.head;
-    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref, h->cur));
+    LAUNCH_K(2, l, h->ops.inject(v.view, v.bnd, v.ring, st, wt, slots, resc, par, ref, nullptr,
+                                 h->cur));
   }
   if (l + 1 < h->nlev) {
     Level& c = h->lev[l + 1];
@@ -852,6 +880,15 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
       v.ring.hist = (float*)v.hist_mem;
       cudaMemsetAsync(v.hist_mem, 0, hb, h->stream);
     }
+    if (const size_t xb = xf_bytes(h, l)) {
+      v.xf_mem = h->dalloc(xb);
+      if (!v.xf_mem) {
+        release(h);
+        delete h;
+        return LBM_ENOMEM;
+      }
+      cudaMemsetAsync(v.xf_mem, 0, xb, h->stream);
+    }
     const size_t db = hrr_du_bytes(h, l), sb = hrr_sh_bytes(h, l);
     if (db) {
       v.du_mem = h->dalloc(db);
@@ -913,7 +950,7 @@ int lbm_bytes(const lbm_config* cfg, unsigned long long* bytes) {
     for (int l = 0; l < h->nlev; ++l) build_view(h, l);
     for (int l = 1; l < h->nlev; ++l) build_interface(h, l);
     for (int l = 0; l < h->nlev; ++l) {
-      total += h->lev[l].bytes + hrr_du_bytes(h, l) + hrr_sh_bytes(h, l);
+      total += h->lev[l].bytes + hrr_du_bytes(h, l) + hrr_sh_bytes(h, l) + xf_bytes(h, l);
       if (l >= 1)
         total += sizeof(float) * 3ull * h->lev[l].ring.nv * h->lev[l].ring.K * h->batch;
     }
@@ -1359,10 +1396,10 @@ int lbm_autotune(lbm_handle h, int reps, int* shapes) {
         if (r == 1) e = cudaEventRecord(e0, h->stream);
         if (e == cudaSuccess)
           e = h->ops.stream_collide(w, h->cfg.collision, h->cfg.storage, 0, om, h->ref, cx, cy,
-                                    h->stream);
+                                    xf_of(h, l), h->stream);
         if (e == cudaSuccess)
           e = h->ops.stream_collide(w, h->cfg.collision, h->cfg.storage, 1, om, h->ref, cx, cy,
-                                    h->stream);
+                                    xf_of(h, l), h->stream);
       }
       if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);

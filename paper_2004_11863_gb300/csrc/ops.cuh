@@ -12,16 +12,19 @@ namespace mlbm {
 struct Ops {
   int q, d;
   // K1: fused stream + collide of every active node of a level.
-  // (bx, by: block shape, bx a multiple of 32, bx * by <= 128)
+  // (bx, by: block shape, bx a multiple of 32, bx * by <= 128; xf: the
+  // level's face buffer, or null when the rebuild writes the planes)
   cudaError_t (*stream_collide)(const LevelView& v, int coll, int storage, int par, float omega,
-                                const RefState& ref, int bx, int by, cudaStream_t s);
+                                const RefState& ref, int bx, int by, const void* xf,
+                                cudaStream_t s);
   // K2: history capture (mode 0) or set-up (mode 1).
   cudaError_t (*capture)(const LevelView& p, const RingDesc& R, int storage, int par, int mode,
                          int s_new, int s_also, const RefState& ref, cudaStream_t s);
-  // K3: coarse -> fine boundary rebuild.
+  // K3: coarse -> fine boundary rebuild (xf: face buffer of the nodes on
+  // faces normal to x, or null: every node into the planes).
   cudaError_t (*inject)(const LevelView& c, const BndDesc& B, const RingDesc& R, int storage,
                         const float* wt, const int* slots, float resc, int par, const RefState& ref,
-                        cudaStream_t s);
+                        void* xf, cudaStream_t s);
   // K4: fine -> coarse restriction.
   cudaError_t (*restrict_tn)(const LevelView& p, const LevelView& c, const TnDesc& T, int storage,
                              float resc, int ppar, int cpar, const RefState& ref, cudaStream_t s);

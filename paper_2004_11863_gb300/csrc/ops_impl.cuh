@@ -35,7 +35,7 @@ RefF make_ref_f(const RefState& r) {
 
 template <class L, class S, int COLL>
 cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx,
-                         int by, cudaStream_t s) {
+                         int by, const S* xf, cudaStream_t s) {
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);
   dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + 2 * by - 1) / (2 * by), v.n[2] * v.batch);
@@ -43,24 +43,24 @@ cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefStat
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
     if (par == 0)
-      k_stream_collide_x2<L, S, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R, xf);
     else
-      k_stream_collide_x2<L, S, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R, xf);
   } else {
     if (par == 0)
-      k_stream_collide_x2<L, S, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R, xf);
     else
-      k_stream_collide_x2<L, S, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_x2<L, S, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R, xf);
   }
   return cudaGetLastError();
 }
 
 template <class L, class S, int COLL>
 cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx, int by,
-                      cudaStream_t s) {
+                      const S* xf, cudaStream_t s) {
   if constexpr ((std::is_same<S, float>::value && K1X2Tune<L>::ON) ||
                 (std::is_same<S, __half>::value && K1X2Tune<L>::ON_H))
-    return sc_x2_launch<L, S, COLL>(v, par, omega, ref, bx, by, s);
+    return sc_x2_launch<L, S, COLL>(v, par, omega, ref, bx, by, xf, s);
   constexpr int NPT = K1Tune<L, S>::NPT;
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);
@@ -69,21 +69,21 @@ cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& 
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
     if (par == 0)
-      k_stream_collide<L, COLL, S, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide<L, COLL, S, 0, true><<<grid, block, 0, s>>>(v, omega, R, xf);
     else
-      k_stream_collide<L, COLL, S, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide<L, COLL, S, 1, true><<<grid, block, 0, s>>>(v, omega, R, xf);
   } else {
     if (par == 0)
-      k_stream_collide<L, COLL, S, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide<L, COLL, S, 0, false><<<grid, block, 0, s>>>(v, omega, R, xf);
     else
-      k_stream_collide<L, COLL, S, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide<L, COLL, S, 1, false><<<grid, block, 0, s>>>(v, omega, R, xf);
   }
   return cudaGetLastError();
 }
 
 template <class L, int COLL>
 cudaError_t sc_pair_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx,
-                           int by, cudaStream_t s) {
+                           int by, const __half* xf, cudaStream_t s) {
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);
   dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + by - 1) / by, v.n[2] * ((v.batch + 1) / 2));
@@ -91,40 +91,42 @@ cudaError_t sc_pair_launch(const LevelView& v, int par, float omega, const RefSt
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
     if (par == 0)
-      k_stream_collide_pair<L, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_pair<L, COLL, 0, true><<<grid, block, 0, s>>>(v, omega, R, xf);
     else
-      k_stream_collide_pair<L, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_pair<L, COLL, 1, true><<<grid, block, 0, s>>>(v, omega, R, xf);
   } else {
     if (par == 0)
-      k_stream_collide_pair<L, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_pair<L, COLL, 0, false><<<grid, block, 0, s>>>(v, omega, R, xf);
     else
-      k_stream_collide_pair<L, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R);
+      k_stream_collide_pair<L, COLL, 1, false><<<grid, block, 0, s>>>(v, omega, R, xf);
   }
   return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t sc_coll(const LevelView& v, int coll, int par, float omega, const RefState& ref,
-                    int bx, int by, cudaStream_t s) {
+                    int bx, int by, const void* xf, cudaStream_t s) {
+  const S* xs = static_cast<const S*>(xf);
   if (std::is_same<S, __half>::value && v.es == 2) {
+    const __half* xh = static_cast<const __half*>(xf);
     switch (coll) {
-      case 0: return sc_pair_launch<L, 0>(v, par, omega, ref, bx, by, s);
-      case 1: return sc_pair_launch<L, 1>(v, par, omega, ref, bx, by, s);
-      default: return sc_pair_launch<L, 2>(v, par, omega, ref, bx, by, s);
+      case 0: return sc_pair_launch<L, 0>(v, par, omega, ref, bx, by, xh, s);
+      case 1: return sc_pair_launch<L, 1>(v, par, omega, ref, bx, by, xh, s);
+      default: return sc_pair_launch<L, 2>(v, par, omega, ref, bx, by, xh, s);
     }
   }
   switch (coll) {
-    case 0: return sc_launch<L, S, 0>(v, par, omega, ref, bx, by, s);
-    case 1: return sc_launch<L, S, 1>(v, par, omega, ref, bx, by, s);
-    default: return sc_launch<L, S, 2>(v, par, omega, ref, bx, by, s);
+    case 0: return sc_launch<L, S, 0>(v, par, omega, ref, bx, by, xs, s);
+    case 1: return sc_launch<L, S, 1>(v, par, omega, ref, bx, by, xs, s);
+    default: return sc_launch<L, S, 2>(v, par, omega, ref, bx, by, xs, s);
   }
 }
 
 template <class L>
 cudaError_t stream_collide(const LevelView& v, int coll, int storage, int par, float omega,
-                           const RefState& ref, int bx, int by, cudaStream_t s) {
-  return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, ref, bx, by, s)
-                      : sc_coll<L, __half>(v, coll, par, omega, ref, bx, by, s);
+                           const RefState& ref, int bx, int by, const void* xf, cudaStream_t s) {
+  return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, ref, bx, by, xf, s)
+                      : sc_coll<L, __half>(v, coll, par, omega, ref, bx, by, xf, s);
 }
 
 template <class L>
@@ -142,7 +144,7 @@ cudaError_t capture(const LevelView& p, const RingDesc& R, int storage, int par,
 template <class L>
 cudaError_t inject(const LevelView& c, const BndDesc& B, const RingDesc& R, int storage,
                    const float* wt, const int* slots, float resc, int par, const RefState& ref,
-                   cudaStream_t s) {
+                   void* xf, cudaStream_t s) {
   if (B.count == 0) return cudaSuccess;
   using T = InjTile<L>;
   InjDesc J{};
@@ -170,20 +172,22 @@ cudaError_t inject(const LevelView& c, const BndDesc& B, const RingDesc& R, int 
     if (storage == 0)
       k_inject_sep<L, float><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0],
                                                     slots[1], slots[2], resc, par,
-                                                    make_ref_f<L>(ref));
+                                                    make_ref_f<L>(ref), static_cast<float*>(xf));
     else
       k_inject_sep<L, __half><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0],
                                                      slots[1], slots[2], resc, par,
-                                                     make_ref_f<L>(ref));
+                                                     make_ref_f<L>(ref), static_cast<__half*>(xf));
     return cudaGetLastError();
   }
   dim3 block(T::TI, T::TJ, T::G);
   if (storage == 0)
     k_inject<L, float><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0], slots[1],
-                                              slots[2], resc, par, make_ref_f<L>(ref));
+                                              slots[2], resc, par, make_ref_f<L>(ref),
+                                              static_cast<float*>(xf));
   else
     k_inject<L, __half><<<grid, block, 0, s>>>(c, J, R, wt[0], wt[1], wt[2], slots[0], slots[1],
-                                               slots[2], resc, par, make_ref_f<L>(ref));
+                                               slots[2], resc, par, make_ref_f<L>(ref),
+                                               static_cast<__half*>(xf));
   return cudaGetLastError();
 }
 

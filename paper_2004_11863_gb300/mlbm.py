@@ -217,6 +217,7 @@ class Lbm:
                           ctypes.byref(h))
         _check(rc, "lbm_create")
         self._h = h
+        self._steps = 0  # coarse steps since the last initial state
 
     @classmethod
     def from_case(cls, case, storage="fp32", batch=1, init=True, **kw):
@@ -250,6 +251,7 @@ class Lbm:
         if rho.size != self.nodes(level) or u.shape[1] != rho.size:
             raise ValueError("field size does not match the level")
         _check(lib().lbm_init(self._h, level, run, _dp(rho), _dp(u)), "lbm_init")
+        self._steps = 0
 
     def init_analytic(self, ic: dict, run=0):
         """Device-side initial state from a workload IC description
@@ -265,6 +267,7 @@ class Lbm:
         d.eps = float(ic.get("eps", 0.0))
         d.drho = float(ic.get("drho", 0.0))
         _check(lib().lbm_init_analytic(self._h, run, ctypes.byref(d)), "lbm_init_analytic")
+        self._steps = 0
 
     def noise(self, single: "Lbm", run=0, margin=4):
         """(max, rms, nodes) of |rho - rho_single| outside the refined box."""
@@ -279,6 +282,11 @@ class Lbm:
 
     def step(self, n=1):
         _check(lib().lbm_step(self._h, int(n)), "lbm_step")
+        self._steps += int(n)
+
+    def coarse_steps(self) -> int:
+        """Coarse steps issued through this object since the last initial state."""
+        return self._steps
 
     def set_graphs(self, enable: bool):
         _check(lib().lbm_set_graphs(self._h, int(bool(enable))), "lbm_set_graphs")

@@ -262,23 +262,33 @@ def pulse_2level_d2q9(collision: str = "RR", steps: int = 1500) -> Case:
                      amplitude=1e-3), steps)
 
 
-def vortex_slab_d3q19(steps: int = 500) -> Case:
-    """Coarse 256^3 D3Q19, fine slab x in [128,256] (y, z periodic), RR,
-    tau_c = 0.5 + 5e-5, vortex column about z, R = 8, at (100, 128)."""
-    return Case("vortex3d", "D3Q19", "RR", 0.5 + 5e-5, (256, 256, 256),
-                [((128, 0, 0), (256, 256, 256))],
-                dict(kind="vortex", u0=(0.1 * CS, 0.0, 0.0), center=(100.0, 128.0),
+def vortex_slab_d3q19(steps: int = 500, side: int = 256) -> Case:
+    """Coarse side^3 D3Q19 (256^3), fine slab x in [side/2, side] (y, z
+    periodic), RR, tau_c = 0.5 + 5e-5, vortex column about z, R = 8, at
+    (side/2 - 28, side/2): (100, 128) at full size, so that the vortex centre
+    reaches the interface after 500 steps at 0.1 c_s.  Smaller sides keep the
+    structure for bounded oracle runs."""
+    name = "vortex3d" if side == 256 else f"vortex3d_{side}"
+    return Case(name, "D3Q19", "RR", 0.5 + 5e-5, (side, side, side),
+                [((side // 2, 0, 0), (side, side, side))],
+                dict(kind="vortex", u0=(0.1 * CS, 0.0, 0.0),
+                     center=(side / 2.0 - 28.0, side / 2.0),
                      radius=8.0, eps=0.05 * CS), steps)
 
 
-def pulse_3level_d3q27(steps: int = 800) -> Case:
-    """Coarse 192^3 D3Q27, level 1 on [48,144]^3 (193^3 nodes), level 2 on
-    the central 48^3 coarse region, i.e. [48,144]^3 in level-1 node units
-    (193^3 nodes), RR, tau_c = 0.5 + 1e-4, pulse A = 1e-3, R = 4 at
-    (132, 96, 96)."""
-    return Case("pulse3d", "D3Q27", "RR", 0.5 + 1e-4, (192, 192, 192),
-                [((48, 48, 48), (144, 144, 144)), ((48, 48, 48), (144, 144, 144))],
-                dict(kind="pulse", center=(132.0, 96.0, 96.0), radius=4.0,
+def pulse_3level_d3q27(steps: int = 800, side: int = 192) -> Case:
+    """Coarse side^3 D3Q27 (192^3), level 1 on the central half [side/4,
+    3 side/4]^3 (193^3 nodes), level 2 on the central half of level 1, i.e.
+    [side/4, 3 side/4]^3 in level-1 node units (193^3 nodes), RR, tau_c =
+    0.5 + 1e-4, pulse A = 1e-3, R = 4 at (side/2 + 3 side/16, side/2,
+    side/2): (132, 96, 96) at full size, inside level 1 and outside level 2.
+    Smaller sides keep the structure for bounded oracle runs."""
+    q = side // 4
+    name = "pulse3d" if side == 192 else f"pulse3d_{side}"
+    return Case(name, "D3Q27", "RR", 0.5 + 1e-4, (side, side, side),
+                [((q, q, q), (3 * q, 3 * q, 3 * q)), ((q, q, q), (3 * q, 3 * q, 3 * q))],
+                dict(kind="pulse", center=(side / 2.0 + 3.0 * side / 16.0, side / 2.0,
+                                           side / 2.0), radius=4.0,
                      amplitude=1e-3), steps)
 
 

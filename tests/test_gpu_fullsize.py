@@ -2,9 +2,12 @@
 configuration bench.py times, against the FP64 oracle element by element.
 
 - vortex2d (coarse 128x64, fine 129x128, RR): the full 400 coarse steps;
-- pulse2d (coarse 512^2, fine 513^2): RR for the full 1500 coarse steps and
-  BGK for 500, as a batch of 33 runs (the benchmark's batch) of which two
-  are compared with the oracle;
+- pulse2d (coarse 512^2, fine 513^2): RR and BGK for the full 1500 coarse
+  steps, as a batch of 33 runs (the benchmark's batch) of which two are
+  compared with the oracle, in binary32 (1e-6) and in binary16 shifted
+  storage (run pairs, the stated bound); and the spurious-noise measure
+  (max over t <= 450 coarse steps of the density difference to the
+  single-level run outside the fine box) against the oracle's;
 - vortex3d (coarse 256^3 + fine 257x512x512, D3Q19 RR) and pulse3d (coarse
   192^3 + two 193^3 levels, D3Q27 RR): 2 coarse steps at full size (the
   oracle needs 26 GB and 12 GB of host memory; skipped with a reason when the
@@ -66,26 +69,116 @@ def test_vortex2d_full_400_steps(M):
     assert dr <= TOL32 and du <= TOL32, (dr, du)
 
 
-@pytest.mark.parametrize("collision,steps", [("RR", 1500), ("BGK", 500)])
-def test_pulse2d_full_in_bench_batch(M, collision, steps):
-    """Runs 0 and 32 of a 33-run batch (the benchmark launch) against the
-    oracle; the other runs carry pulses at other places."""
-    case = W.pulse_2level_d2q9(collision, steps=steps)
+_ORACLE = {}
+
+
+def oracle_pulse2d(collision, steps=1500):
+    """The oracle's pulse2d run after `steps` coarse steps (computed once per
+    session, shared by the binary32 and binary16 checks)."""
+    key = (collision, steps)
+    if key not in _ORACLE:
+        o = oracle.Run.from_case(W.pulse_2level_d2q9(collision, steps=steps))
+        o.step(steps)
+        _ORACLE[key] = o
+    return _ORACLE[key]
+
+
+def pulse2d_batch(M, case, storage):
+    """The benchmark's 33-run batch: runs 0 and 32 carry the workload's
+    pulse, the others a pulse at another place."""
     other = case.with_(ic=dict(kind="pulse", center=(300.0, 200.0, 0.0), radius=6.0,
                                amplitude=1e-3))
     g = M.Lbm(case.lattice, case.collision, case.tau0, case.dims, case.boxes,
-              batch=BENCH_BATCH)
+              storage=storage, batch=BENCH_BATCH)
     for l in range(2):
         f0 = W.initial_fields(case, l)
         f1 = W.initial_fields(other, l)
         for b in range(BENCH_BATCH):
             g.init(l, b, *(f0 if b in (0, BENCH_BATCH - 1) else f1))
+    g.autotune(reps=2)
+    return g
+
+
+def fp16_bound(case):
+    """Stated error bound of binary16 shifted storage (derivation in
+    test_gpu_parity.fp16_bound): 2 q^(1/2) 2^-11 gmax n^(1/2), gmax the
+    largest stored deviation of the initial state, n the finest-level
+    updates."""
+    from tests.test_gpu_parity import fp16_bound as b
     o = oracle.Run.from_case(case)
-    g.step(steps)
-    o.step(steps)
+    try:
+        return b(case, o)
+    finally:
+        o.close()
+
+
+@pytest.mark.parametrize("collision", ["RR", "BGK"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_pulse2d_full_in_bench_batch(M, collision, storage):
+    """Runs 0 and 32 of a 33-run batch (the benchmark launch) against the
+    oracle after the full 1500 coarse steps; binary16 batches are stored as
+    interleaved run pairs (run 32 is the first of the last, half-empty
+    pair)."""
+    case = W.pulse_2level_d2q9(collision, steps=1500)
+    tol = TOL32 if storage == "fp32" else fp16_bound(case)
+    g = pulse2d_batch(M, case, storage)
+    g.step(case.steps)
+    o = oracle_pulse2d(collision, case.steps)
     for run in (0, BENCH_BATCH - 1):
         dr, du = max_err(g, o, 2, run)
-        assert dr <= TOL32 and du <= TOL32, (run, dr, du)
+        print(f"pulse2d {collision} {storage} run {run}: max|drho| {dr:.3e} max|du| {du:.3e} "
+              f"(bound {tol:.3e})")
+        assert dr <= tol and du <= tol, (run, dr, du, tol)
+    g.close()
+
+
+def _noise_max(case, r2, r1, margin):
+    """R23 noise measure on the host (the definition lbm_noise reduces on
+    the device): max |rho_2lev - rho_1lev| over level-0 nodes outside the
+    fine box grown by `margin` cells."""
+    from tests.test_gpu_features import _noise_numpy
+    return float(_noise_numpy(case, r2, r1, margin)[0])
+
+
+def test_pulse2d_noise_measure_per_precision_and_collision(M):
+    """Spurious-noise measure of the acoustic-pulse workload (the density
+    difference between the two-level run and the same state on the uniform
+    coarse grid, outside the fine box by >= 4 cells), sampled every 5
+    coarse steps up to t = 450 (before the transmitted wave leaves the fine
+    box), maximum over the samples: binary32 and binary16 storage, BGK and
+    RR, against the FP64 oracle's value.  binary32 within 1e-6; binary16
+    within the stated storage bound."""
+    T, every, margin = 450, 5, 4
+    rows = []
+    for collision in ("BGK", "RR"):
+        case = W.pulse_2level_d2q9(collision, steps=T)
+        single = case.with_(boxes=[])
+        o2 = oracle.Run.from_case(case)
+        o1 = oracle.Run.from_case(single)
+        onoise = 0.0
+        for _ in range(T // every):
+            o2.step(every)
+            o1.step(every)
+            onoise = max(onoise, _noise_max(case, o2.macros(0)[0], o1.macros(0)[0], margin))
+        o2.close()
+        o1.close()
+        for storage in ("fp32", "fp16"):
+            g2 = M.Lbm.from_case(case, storage=storage)
+            g1 = M.Lbm.from_case(single, storage=storage)
+            gnoise = 0.0
+            for _ in range(T // every):
+                g2.step(every)
+                g1.step(every)
+                gnoise = max(gnoise, g2.noise(g1, margin=margin)[0])
+            g2.close()
+            g1.close()
+            tol = TOL32 if storage == "fp32" else 2 * fp16_bound(case)
+            rows.append((collision, storage, gnoise, onoise, tol))
+    for c, st, gn, on, tol in rows:
+        print(f"noise R23 pulse2d {c} {st}: GPU {gn:.6e} oracle {on:.6e} "
+              f"diff {abs(gn - on):.2e} (tolerance {tol:.2e})")
+    for c, st, gn, on, tol in rows:
+        assert gn > 0 and abs(gn - on) <= tol, (c, st, gn, on, tol)
 
 
 def _full3d(M, case, need_gb, steps=2):

@@ -1,0 +1,107 @@
+"""Long 3D runs against the FP64 oracle at the workloads' full step counts.
+
+The two 3D workloads have the oracle's cost far beyond a test session at
+full size, so they are checked at the same structure and a reduced size for
+their full step counts (the interface error has hundreds of coarse steps to
+grow), against oracle results stored by ``tests/golden/make_oracle_golden.py``
+(a script that calls only the oracle):
+
+- vortex3d_64: D3Q19 RR, coarse 64^3 with the fine slab x in [32, 64]
+  (65 x 128 x 128), the vortex column crossing the slab's faces, 500 coarse
+  steps;
+- pulse3d_96: D3Q27 RR, coarse 96^3 with two nested central boxes (97^3
+  nodes each), the pulse crossing both interfaces, 800 coarse steps.
+
+Checked, binary32 storage: every node of one plane per level through the
+flow feature (it crosses every interface of the level) and 2048 seeded
+random active nodes per level, |drho|, |du| <= 1e-6; and the FP64
+conservation sums of lbm_diag against the oracle's sums over all active
+nodes of each level.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2004_11863_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+CASES = {
+    "vortex3d_64": lambda: W.vortex_slab_d3q19(steps=500, side=64),
+    "pulse3d_96": lambda: W.pulse_3level_d3q27(steps=800, side=96),
+}
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2004_11863_gb300 import build
+    build.build()
+    from paper_2004_11863_gb300 import mlbm
+    return mlbm
+
+
+@pytest.fixture(scope="module")
+def runs(M):
+    """Each case stepped on the GPU for its full step count (autotuned block
+    shapes, as the benchmark launches it), with its stored oracle result."""
+    out = {}
+    for name, mk in CASES.items():
+        case = mk()
+        gold = np.load(os.path.join(GOLDEN, f"oracle_{name}_{case.steps}.npz"))
+        assert int(gold["steps"]) == case.steps
+        g = M.Lbm.from_case(case)
+        g.autotune(reps=2)
+        g.step(case.steps)
+        out[name] = (case, g, gold)
+    yield out
+    for _, g, _ in out.values():
+        g.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sampled_nodes_match_oracle(runs, name):
+    case, g, gold = runs[name]
+    for l in range(case.nlevels):
+        rho, u = g.macros(l)
+        for tag in ("plane", "rand"):
+            idx = gold[f"L{l}_{tag}_idx"]
+            act = ~np.isnan(rho[idx])
+            ref_r = gold[f"L{l}_{tag}_drho"].astype(np.float64)
+            ref_u = gold[f"L{l}_{tag}_u"].astype(np.float64)
+            # the oracle's inactive nodes are NaN there too: same node sets
+            assert np.array_equal(act, ~np.isnan(ref_r)), (l, tag)
+            dr = np.max(np.abs(rho[idx][act] - case.rho0 - ref_r[act]))
+            du = np.max(np.abs(u[:, idx][:, act] - ref_u[:, act]))
+            assert dr <= TOL32 and du <= TOL32, (name, l, tag, dr, du)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_conservation_sums_match_oracle(runs, name):
+    """lbm_diag's FP64 sums of (rho - rho0) and rho u over each level's
+    active nodes against the oracle's, within 1e-9 of the level's total
+    mass rho0 N (relative): the per-node binary32 differences (<= 1e-6)
+    average out over the level instead of adding up."""
+    case, g, gold = runs[name]
+    mass, mom, ok = g.diag()
+    assert ok
+    for l in range(case.nlevels):
+        N = int(gold[f"L{l}_active"])
+        scale = case.rho0 * N
+        dm = abs(mass[l] - float(gold[f"L{l}_mass"]))
+        dp = float(np.max(np.abs(mom[l] - gold[f"L{l}_mom"])))
+        assert dm <= 1e-9 * scale and dp <= 1e-9 * scale, (name, l, dm, dp, scale)
+        # and the device reduction against the host sum of the GPU's own fields
+        rho, u = g.macros(l)
+        act = ~np.isnan(rho)
+        assert int(act.sum()) == N
+        hm = float(np.sum(rho[act] - case.rho0))
+        hp = np.sum(rho[act][None, :] * u[:, act], axis=1)
+        assert abs(mass[l] - hm) <= 1e-12 * scale
+        assert float(np.max(np.abs(mom[l] - hp))) <= 1e-12 * scale

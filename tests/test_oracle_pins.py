@@ -431,6 +431,101 @@ def test_smooth_wave_crosses_interface_like_uniform_grid(coll):
     assert err < 2e-6, err  # 2% of the 1e-4 amplitude
 
 
+# ------------------------------------------- 3D interface geometry (R8, R9)
+
+def _active(r, level):
+    """Active nodes from the node classes (not from the fields, so that a
+    run that went unstable fails the checks instead of masking itself)."""
+    return r.classes(level) != 0
+
+
+@pytest.mark.parametrize("lat,coll", [("D3Q19", "RR"), ("D3Q27", "BGK")])
+def test_shear_wave_across_closed_3d_box(lat, coll):
+    """u_x = U sin(k y) sin(k z) (an exact decaying solution: divergence
+    free, no advection) around a closed refined box, so that the rebuilt
+    outer layer interpolates a field that varies along both tangent axes of
+    the x-normal faces (face-centre nodes: the tensor-product cubic of
+    eq. spaceInt, reading R9) and along one tangent of the other faces, and
+    the restriction filters it in 3D (eq. filterFneq as a tensor product,
+    reading R8).  Every level must follow U exp(-2 nu_c k^2 t) sin sin
+    pointwise within 1 % of the amplitude, stay uniform along x within
+    0.25 %, keep u_y, u_z below 0.3 % of it, and rescale the off-equilibrium stress as a1^f / a1^c =
+    tau_f / (2 tau_c) (eqs. rescNu, fneqResc).  A tap along the wrong axis,
+    a wrong offset or weight in the face-centre stencil, or a wrong 3D
+    filter footprint breaks the pointwise and uniformity checks."""
+    L, lo, hi, tau, T, U = 48, 12, 36, 0.6, 200, 1e-4
+    k = 2 * math.pi / L
+    c = W.Case("shear3d", lat, coll, tau, (L, L, L), [((lo,) * 3, (hi,) * 3)],
+               dict(kind="uniform"), 0)
+    r = oracle.Run(c.lattice, c.collision, c.tau0, c.dims, c.boxes)
+    for l in range(r.nlevels):
+        X, Y, Z = W.level_coords(c, l)
+        u = np.zeros((3, X.size))
+        u[0] = U * np.sin(k * Y) * np.sin(k * Z)
+        r.init_level(l, np.ones(X.size), u)
+    r.init_done()
+    r.step(T)
+    want = U * math.exp(-CS2 * (tau - 0.5) * 2 * k * k * T)
+    for l in range(r.nlevels):
+        rho, u = r.macros(l)
+        X, Y, Z = W.level_coords(c, l)
+        m = _active(r, l)
+        phi = np.sin(k * Y[m]) * np.sin(k * Z[m])
+        amp = np.sum(u[0][m] * phi) / np.sum(phi * phi)
+        assert abs(amp / want - 1) < 0.01, (l, amp, want)
+        assert np.max(np.abs(u[0][m] - want * phi)) < 0.01 * want, l
+        # (the correct scheme keeps u_y, u_z below 0.09 % and the spread along
+        # x below 0.1 % of the amplitude here)
+        assert np.max(np.abs(u[1:, m])) < 0.003 * want, l
+        n = r.dims(l)[0]
+        ux = u[0].reshape(n[2], n[1], n[0])
+        mm = m.reshape(n[2], n[1], n[0])
+        spread = max(np.ptp(ux[zz, yy][mm[zz, yy]]) for zz in range(n[2]) for yy in range(n[1])
+                     if mm[zz, yy].any())
+        assert spread < 0.0025 * want, (l, spread)
+    tau_f = r.tau(1)
+    for comp, (yy, zz) in ((1, (24, 18)), (2, (18, 24))):  # a1_xy, a1_xz
+        a1 = []
+        for l, t, xs in ((0, tau, 4.0), (1, tau_f, 24.0)):
+            f = r.populations(l)
+            X, Y, Z = W.level_coords(c, l)
+            idx = np.nonzero((np.abs(X - xs) < 1e-9) & (np.abs(Y - yy) < 1e-9)
+                             & (np.abs(Z - zz) < 1e-9))[0][0]
+            a1.append(oracle.a1(lat, f[:, idx])[0, comp] / (1 - 1 / t))
+        assert abs((a1[1] / a1[0]) / (tau_f / (2 * tau)) - 1) < 0.01, (comp, a1)
+
+
+@pytest.mark.parametrize("lat,boxes", [
+    ("D3Q19", [((12, 12, 12), (36, 36, 36))]),
+    ("D3Q27", [((12, 12, 12), (36, 36, 36)), ((12, 12, 12), (36, 36, 36))]),
+], ids=["D3Q19_two_levels", "D3Q27_three_levels"])
+def test_oblique_acoustic_wave_crosses_closed_box_like_uniform_grid(lat, boxes):
+    """A plane acoustic wave travelling along (1, 1, 1), oblique to every
+    axis, crosses a closed refined box (nested twice for D3Q27) -- every
+    face, edge and corner of the rebuilt layer and of the restriction ring
+    -- and must agree with the same wave on the uniform coarse grid within
+    2 % of its amplitude on every coarse node after it has passed (Sec. 4:
+    temporal and spatial interpolation, filter and both rescalings
+    consistent in 3D)."""
+    L, tau, T, A = 48, 0.52, 60, 1e-4
+    kv = 2 * math.pi / L * np.ones(3)
+    kh = kv / np.linalg.norm(kv)
+    res = []
+    for bx in ([], boxes):
+        c = W.Case("ac3d", lat, "RR", tau, (L, L, L), bx, dict(kind="uniform"), 0)
+        r = oracle.Run(c.lattice, c.collision, c.tau0, c.dims, c.boxes)
+        for l in range(r.nlevels):
+            X, Y, Z = W.level_coords(c, l)
+            ph = np.sin(kv[0] * X + kv[1] * Y + kv[2] * Z)
+            r.init_level(l, 1 + A * ph, A * W.CS * ph[None, :] * kh[:, None])
+        r.init_done()
+        r.step(T)
+        res.append((r.macros(0)[0], _active(r, 0)))
+    m = res[1][1]
+    err = np.max(np.abs(res[1][0][m] - res[0][0][m]))
+    assert err < 0.02 * A, err
+
+
 # ------------------------------------------------------ printed outcome check
 
 def e5_case(collision):

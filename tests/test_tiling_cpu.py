@@ -266,3 +266,69 @@ def test_restriction_tiles_benchmark_layouts(name, mk):
 def test_rebuild_taps_test_layouts(name, case):
     *_, iti, itj = tile_constants()
     check_rebuild_3d(case, iti, itj)
+
+
+def check_face_buffer(case, batch=1, es=1):
+    """Replays the face buffer's index arithmetic: the rebuild writes every
+    node of the two faces normal to a bounded x axis (and only those) once
+    per direction and run, inside the buffer; the level update's warps that
+    take the face path are exactly those holding x = 0 or x = n[0] - 1, for
+    every block width the autotuner tries, and read back the same slots."""
+    D, L = levels(case)
+    q = case.q
+    for l in range(1, len(L)):
+        c = L[l]
+        if not c["boxed"][0]:
+            continue
+        n = c["n"]
+        F = n[1] * n[2]
+        runs = -(-batch // es) * es
+        size = runs * 2 * q * F
+        written = {}
+        # the rebuild: x-face tiles (t1 = y, t2 = z), every node of the face
+        for side in range(2):
+            x = n[0] - 1 if side else 0
+            for z in range(n[2]):
+                for y in range(n[1]):
+                    for r in range(batch):
+                        base = ((((r // es) * 2 + side) * q) * F + z * n[1] + y) * es + r % es
+                        for i in range(q):
+                            e = base + i * F * es
+                            assert 0 <= e < size
+                            assert e not in written
+                            written[e] = (r, x, y, z, i)
+        assert len(written) == batch * 2 * F * q
+        # the update: face warps and the slots each face lane reads
+        for bx in (32, 64, 128):
+            nbx = -(-n[0] // bx)
+            face_lanes = set()
+            for bxi in range(nbx):
+                for w in range(bx // 32):
+                    xw = bxi * bx + 32 * w
+                    if xw >= n[0]:
+                        continue
+                    has = xw == 0 or (xw <= n[0] - 1 < xw + 32)
+                    lanes = [x for x in range(xw, min(xw + 32, n[0])) if x in (0, n[0] - 1)]
+                    assert has == bool(lanes)
+                    face_lanes.update(lanes)
+            assert face_lanes == {0, n[0] - 1}
+        for r in range(batch):
+            for x in (0, n[0] - 1):
+                side = int(x != 0)
+                for z in range(0, n[2], max(1, n[2] // 7)):
+                    for y in range(0, n[1], max(1, n[1] // 7)):
+                        for i in range(q):
+                            e = ((((r // es) * 2 + side) * q + i) * F + z * n[1] + y) * es + r % es
+                            assert written[e] == (r, x, y, z, i)
+
+
+@pytest.mark.parametrize("name,case", LAYOUTS, ids=[n for n, _ in LAYOUTS])
+def test_face_buffer_test_layouts(name, case):
+    check_face_buffer(case, batch=3, es=1)
+    check_face_buffer(case, batch=3, es=2)
+
+
+@pytest.mark.parametrize("name,mk", [(k, v) for k, v in BENCH if k in ("pulse2d", "vortex2d")],
+                         ids=["pulse2d", "vortex2d"])
+def test_face_buffer_benchmark_layouts(name, mk):
+    check_face_buffer(mk(), batch=1, es=1)
