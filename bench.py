@@ -132,7 +132,8 @@ class ClockSampler:
 def workload_case(name: str):
     """A workload by name: pulse2d[_bgk], vortex2d, vortex3d, pulse3d; a
     suffix _<side> gives a 3D workload's structure at a smaller coarse side
-    (e.g. vortex3d_64)."""
+    (e.g. vortex3d_64); vortex3d_yz<n> keeps the full-size rows (x) with n
+    coarse nodes along y and z (profiling captures of the same kernels)."""
     if name == "pulse2d":
         return W.pulse_2level_d2q9("RR")
     if name == "pulse2d_bgk":
@@ -140,6 +141,8 @@ def workload_case(name: str):
     if name == "vortex2d":
         return W.vortex_2level_d2q9()
     base, _, side = name.partition("_")
+    if base == "vortex3d" and side.startswith("yz"):  # full-width rows, shorter y, z
+        return W.vortex_slab_d3q19(side=256, yz=int(side[2:]))
     if base == "vortex3d":
         return W.vortex_slab_d3q19(side=int(side) if side else 256)
     if base == "pulse3d":

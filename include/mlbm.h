@@ -313,6 +313,18 @@ int lbm_autotune(lbm_handle h, int reps, int* shapes);
  * bx * by <= 128.  LBM_EINVAL otherwise.  Synchronises. */
 int lbm_set_block_shape(lbm_handle h, int level, int bx, int by);
 
+/* Face buffers of the 3D levels whose x axis is bounded by their box: on
+ * (1, the default) or off (0).  On: the coarse -> fine rebuild of the
+ * nodes on the two faces normal to x writes their populations into a
+ * compact face buffer (whole 32-byte sectors; in the population planes x is
+ * the fastest axis, so each of those populations would fill a sector of
+ * its own) and the level update reads them from there.  Off: the rebuild
+ * writes them into the planes.  Results are bitwise the same either way.
+ * Not used by the hybrid collision or on levels with sensors on.
+ * Synchronises. */
+int lbm_set_face_buffer(lbm_handle h, int enable);
+
+
 /* Non-hydrodynamic mode sensors of Sec. 7 on one level (all runs), from the
  * next coarse step on: at every iteration of the level, from its
  * pre-collision state at middle nodes (not inactive, not TN, not on a

@@ -268,9 +268,13 @@ struct StripAddr {
 // (y fastest), written and read in whole sectors.  Element of run r,
 // side s, direction i, face node (y, z):
 //   ((((r / es) * 2 + s) * q + i) * F + z * n[1] + y) * es + r % es,
-// F = n[1] * n[2].  The level update reads a face node's populations from
+// F = n[1] * n[2].  (3D levels only: a 2D face holds n[1] nodes of q = 9
+// populations, where the scattered stores cost little.)  The level update
+// reads a face node's populations from
 // here; a warp holds such a node only if it covers x = 0 or x = n[0] - 1,
-// and only those warps take the selecting loads (a warp-uniform branch).
+// and only those warps load from the face buffer (a warp-uniform branch
+// after the loads every lane issues from the planes, so that the other
+// warps run the same code as without face buffers).
 __device__ __forceinline__ bool warp_has_xface(const LevelView& v, const void* xf) {
   const int xw = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   return xf != nullptr && (xw == 0 || (xw <= v.n[0] - 1 && v.n[0] - 1 < xw + 32));
@@ -280,14 +284,21 @@ __device__ __forceinline__ bool warp_has_xface(const LevelView& v, const void* x
 // consecutive x of NPT rows.  All loads of the thread's nodes are issued
 // before the first collision.  The block shape (blockDim.x a multiple of 32,
 // blockDim.x * blockDim.y <= 128) is chosen at run time (lbm_autotune); it
-// changes which nodes share a block, not any node's arithmetic.  FACE: the
-// warp holds a node of a face normal to x, whose populations come from the
-// face buffer xf.
-template <class L, int COLL, class S, int PAR, bool MOV, bool FACE>
-__device__ __forceinline__ void stream_collide_body(const LevelView& v, float omega,
-                                                    const RefF& R, const S* __restrict__ xf,
-                                                    int x, int y0, int z, int run) {
+// changes which nodes share a block, not any node's arithmetic.
+template <class L, int COLL, class S, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
+                                           : (PAR == 0 ? K1Tune<L, S>::MINB_EVEN
+                                                       : K1Tune<L, S>::MINB))
+    k_stream_collide(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
   constexpr int NPT = K1Tune<L, S>::NPT;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * NPT;
+  int z = blockIdx.z, run = 0;
+  if (v.batch > 1) {
+    run = z / v.n[2];
+    z -= run * v.n[2];
+  }
+  if (x >= v.n[0] || y0 >= v.n[1]) return;
   S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
   StripAddr<NPT> a;
   const int off = (int)v.off;
@@ -310,15 +321,11 @@ __device__ __forceinline__ void stream_collide_body(const LevelView& v, float om
     if (v.per[1]) yy = wrapi(yy, v.n[1]);
     a.yo[r] = yy * v.SX;
   }
-  // face buffer of this lane's nodes (FACE warps only)
-  bool fx = false;
-  const S* xb = nullptr;
-  long long F = 0;
-  if constexpr (FACE) {
-    fx = x == 0 || x == v.n[0] - 1;
-    F = (long long)v.n[1] * v.n[2];
-    xb = xf + ((long long)run * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1] + y0;
-  }
+  // a lane on a face normal to x takes its populations from the face buffer:
+  // every lane loads from the planes, then only warps holding such a lane
+  // (a warp-uniform branch) replace that lane's values by the face buffer's
+  const bool fw = warp_has_xface(v, xf);
+  const bool fx = fw && (x == 0 || x == v.n[0] - 1);
   bool ok[NPT];
   float g[NPT][L::Q];
 #pragma unroll
@@ -327,18 +334,27 @@ __device__ __forceinline__ void stream_collide_body(const LevelView& v, float om
     if (ok[k]) {
       sfor<L::Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if constexpr (FACE) {
-          if (fx) {
-            g[k][i] = Store<S>::ld(xb + i * F + k);
-            return;
-          }
-        }
         if constexpr (PAR == 0)
           g[k][i] = Store<S>::ld(f + (long long)i * v.plane + a.at(k, 0, 0, 0));
         else
           g[k][i] = Store<S>::ld(f + (long long)opp<L>(i) * v.plane +
                                  a.at(k, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2)));
       });
+    }
+  }
+  if constexpr (L::D == 3) {  // (2D levels have no face buffer)
+    if (fw && fx) {
+      const long long F = (long long)v.n[1] * v.n[2];
+      const S* xb =
+          xf + ((long long)run * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1] + y0;
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        if (!ok[k]) continue;
+        sfor<L::Q>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          g[k][i] = Store<S>::ld(xb + i * F + k);
+        });
+      }
     }
   }
 #pragma unroll
@@ -353,26 +369,6 @@ __device__ __forceinline__ void stream_collide_body(const LevelView& v, float om
                      val);
     });
   }
-}
-
-template <class L, int COLL, class S, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
-                                           : (PAR == 0 ? K1Tune<L, S>::MINB_EVEN
-                                                       : K1Tune<L, S>::MINB))
-    k_stream_collide(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
-  constexpr int NPT = K1Tune<L, S>::NPT;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * NPT;
-  int z = blockIdx.z, run = 0;
-  if (v.batch > 1) {
-    run = z / v.n[2];
-    z -= run * v.n[2];
-  }
-  if (x >= v.n[0] || y0 >= v.n[1]) return;
-  if (warp_has_xface(v, xf))
-    stream_collide_body<L, COLL, S, PAR, MOV, true>(v, omega, R, xf, x, y0, z, run);
-  else
-    stream_collide_body<L, COLL, S, PAR, MOV, false>(v, omega, R, xf, x, y0, z, run);
 }
 
 // Level update, two nodes per thread in one two-lane collision: the nodes
@@ -444,65 +440,6 @@ struct K1X2Tune<D3Q27> {
   static constexpr int MINB_H = K1X2H_MINB_D3Q27;
 };
 
-template <class L, class S, int COLL, int PAR, bool MOV, bool FACE>
-__device__ __forceinline__ void stream_collide_x2_body(const LevelView& v, float omega,
-                                                       const RefF& R, const S* __restrict__ xf,
-                                                       int x, int y0, int z, int run, bool ok0,
-                                                       bool ok1) {
-  S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
-  // each lane's node; an idle lane reads its partner's
-  const NodeAddr a0 = node_addr<L>(v, x, ok0 ? y0 : y0 + 1, z);
-  const NodeAddr a1 = node_addr<L>(v, x, ok1 ? y0 + 1 : y0, z);
-  // face buffer of this lane's nodes (FACE warps only)
-  bool fx = false;
-  const S* xb0 = nullptr;
-  const S* xb1 = nullptr;
-  long long F = 0;
-  if constexpr (FACE) {
-    fx = x == 0 || x == v.n[0] - 1;
-    F = (long long)v.n[1] * v.n[2];
-    const S* xb = xf + ((long long)run * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1];
-    xb0 = xb + (ok0 ? y0 : y0 + 1);
-    xb1 = xb + (ok1 ? y0 + 1 : y0);
-  }
-  // element offsets are formed whole before indexing (f[i * plane + at]):
-  // per-direction base pointers would cost 64-bit registers per direction
-  F2 g[L::Q];
-  sfor<L::Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    if constexpr (FACE) {
-      if (fx) {
-        g[i].v.x = Store<S>::ld(xb0 + i * F);
-        g[i].v.y = Store<S>::ld(xb1 + i * F);
-        return;
-      }
-    }
-    if constexpr (PAR == 0) {
-      g[i].v.x = Store<S>::ld(&f[(long long)i * v.plane + a0.at(0, 0, 0)]);
-      g[i].v.y = Store<S>::ld(&f[(long long)i * v.plane + a1.at(0, 0, 0)]);
-    } else {
-      g[i].v.x = Store<S>::ld(
-          &f[(long long)opp<L>(i) * v.plane + a0.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
-      g[i].v.y = Store<S>::ld(
-          &f[(long long)opp<L>(i) * v.plane + a1.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
-    }
-  });
-  collide_emit_x2<L, COLL, MOV>(g, omega, R, [&](auto I, F2 val) {
-    constexpr int i = decltype(I)::value;
-    if constexpr (PAR == 0) {
-      if (ok0) Store<S>::st(&f[(long long)opp<L>(i) * v.plane + a0.at(0, 0, 0)], val.v.x);
-      if (ok1) Store<S>::st(&f[(long long)opp<L>(i) * v.plane + a1.at(0, 0, 0)], val.v.y);
-    } else {
-      if (ok0)
-        Store<S>::st(&f[(long long)i * v.plane + a0.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))],
-                     val.v.x);
-      if (ok1)
-        Store<S>::st(&f[(long long)i * v.plane + a1.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))],
-                     val.v.y);
-    }
-  });
-}
-
 template <class L, class S, int COLL, int PAR, bool MOV>
 __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
                                                                       : K1X2Tune<L>::MINB_H)
@@ -518,11 +455,57 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<
   const bool ok0 = y0 < v.n[1] && !inactive(v, x, y0, z);
   const bool ok1 = y0 + 1 < v.n[1] && !inactive(v, x, y0 + 1, z);
   if (!ok0 && !ok1) return;
-  if (warp_has_xface(v, xf))
-    stream_collide_x2_body<L, S, COLL, PAR, MOV, true>(v, omega, R, xf, x, y0, z, run, ok0, ok1);
-  else
-    stream_collide_x2_body<L, S, COLL, PAR, MOV, false>(v, omega, R, xf, x, y0, z, run, ok0,
-                                                        ok1);
+  S* f = static_cast<S*>(v.f) + run * v.run_stride;  // es = 1 for this kernel
+  // each lane's node; an idle lane reads its partner's
+  const NodeAddr a0 = node_addr<L>(v, x, ok0 ? y0 : y0 + 1, z);
+  const NodeAddr a1 = node_addr<L>(v, x, ok1 ? y0 + 1 : y0, z);
+  // a lane on a face normal to x takes its populations from the face buffer:
+  // every lane loads from the planes, then only warps holding such a lane
+  // (a warp-uniform branch) replace that lane's values by the face buffer's
+  const bool fw = warp_has_xface(v, xf);
+  const bool fx = fw && (x == 0 || x == v.n[0] - 1);
+  // element offsets are formed whole before indexing (f[i * plane + at]):
+  // per-direction base pointers would cost 64-bit registers per direction
+  F2 g[L::Q];
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (PAR == 0) {
+      g[i].v.x = Store<S>::ld(&f[(long long)i * v.plane + a0.at(0, 0, 0)]);
+      g[i].v.y = Store<S>::ld(&f[(long long)i * v.plane + a1.at(0, 0, 0)]);
+    } else {
+      g[i].v.x = Store<S>::ld(
+          &f[(long long)opp<L>(i) * v.plane + a0.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
+      g[i].v.y = Store<S>::ld(
+          &f[(long long)opp<L>(i) * v.plane + a1.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
+    }
+  });
+  if constexpr (L::D == 3) {  // (2D levels have no face buffer)
+    if (fw && fx) {
+      const long long F = (long long)v.n[1] * v.n[2];
+      const S* xb = xf + ((long long)run * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1];
+      const S* xb0 = xb + (ok0 ? y0 : y0 + 1);
+      const S* xb1 = xb + (ok1 ? y0 + 1 : y0);
+      sfor<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        g[i].v.x = Store<S>::ld(xb0 + i * F);
+        g[i].v.y = Store<S>::ld(xb1 + i * F);
+      });
+    }
+  }
+  collide_emit_x2<L, COLL, MOV>(g, omega, R, [&](auto I, F2 val) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (PAR == 0) {
+      if (ok0) Store<S>::st(&f[(long long)opp<L>(i) * v.plane + a0.at(0, 0, 0)], val.v.x);
+      if (ok1) Store<S>::st(&f[(long long)opp<L>(i) * v.plane + a1.at(0, 0, 0)], val.v.y);
+    } else {
+      if (ok0)
+        Store<S>::st(&f[(long long)i * v.plane + a0.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))],
+                     val.v.x);
+      if (ok1)
+        Store<S>::st(&f[(long long)i * v.plane + a1.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))],
+                     val.v.y);
+    }
+  });
 }
 
 // Level update of binary16 storage with runs interleaved in pairs (es = 2):
@@ -556,51 +539,6 @@ struct K1PairTune<D3Q27> {
   static constexpr int MINB = K1P_MINB_D3Q27;
 };
 
-template <class L, int COLL, int PAR, bool MOV, bool FACE>
-__device__ __forceinline__ void stream_collide_pair_body(const LevelView& v, float omega,
-                                                         const RefF& R,
-                                                         const __half* __restrict__ xf, int x,
-                                                         int y, int z, int pair) {
-  // half2 units: a plane is plane / 2 of them, node e sits at e
-  __half2* f = reinterpret_cast<__half2*>(static_cast<__half*>(v.f) + pair * v.run_stride);
-  const long long ph = v.plane / 2;
-  const NodeAddr a = node_addr<L>(v, x, y, z);
-  bool fx = false;
-  const __half2* xb = nullptr;
-  long long F = 0;
-  if constexpr (FACE) {
-    fx = x == 0 || x == v.n[0] - 1;
-    F = (long long)v.n[1] * v.n[2];
-    xb = reinterpret_cast<const __half2*>(xf) + ((long long)pair * 2 + (x != 0)) * L::Q * F +
-         (long long)z * v.n[1] + y;
-  }
-  F2 g[L::Q];  // lane x: run 2p, lane y: run 2p+1
-  sfor<L::Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    __half2 h;
-    if constexpr (FACE) {
-      if (fx) {
-        h = xb[i * F];
-        g[i].v = __half22float2(h);
-        return;
-      }
-    }
-    if constexpr (PAR == 0)
-      h = f[i * ph + a.at(0, 0, 0)];
-    else
-      h = f[opp<L>(i) * ph + a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))];
-    g[i].v = __half22float2(h);
-  });
-  collide_emit_x2<L, COLL, MOV>(g, omega, R, [&](auto I, F2 val) {
-    constexpr int i = decltype(I)::value;
-    const __half2 h = __float22half2_rn(val.v);
-    if constexpr (PAR == 0)
-      f[opp<L>(i) * ph + a.at(0, 0, 0)] = h;
-    else
-      f[i * ph + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))] = h;
-  });
-}
-
 template <class L, int COLL, int PAR, bool MOV>
 __global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
     k_stream_collide_pair(LevelView v, float omega, RefF R, const __half* __restrict__ xf) {
@@ -613,10 +551,43 @@ __global__ void __launch_bounds__(128, K1PairTune<L>::MINB)
     z -= pair * v.n[2];
   }
   if (x >= v.n[0] || y >= v.n[1] || inactive(v, x, y, z)) return;
-  if (warp_has_xface(v, xf))
-    stream_collide_pair_body<L, COLL, PAR, MOV, true>(v, omega, R, xf, x, y, z, pair);
-  else
-    stream_collide_pair_body<L, COLL, PAR, MOV, false>(v, omega, R, xf, x, y, z, pair);
+  // half2 units: a plane is plane / 2 of them, node e sits at e
+  __half2* f = reinterpret_cast<__half2*>(static_cast<__half*>(v.f) + pair * v.run_stride);
+  const long long ph = v.plane / 2;
+  const NodeAddr a = node_addr<L>(v, x, y, z);
+  // a lane on a face normal to x takes its populations from the face buffer
+  // (after the loads from the planes, in warps holding such a lane only)
+  const bool fw = warp_has_xface(v, xf);
+  const bool fx = fw && (x == 0 || x == v.n[0] - 1);
+  F2 g[L::Q];  // lane x: run 2p, lane y: run 2p+1
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    __half2 h;
+    if constexpr (PAR == 0)
+      h = f[i * ph + a.at(0, 0, 0)];
+    else
+      h = f[opp<L>(i) * ph + a.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))];
+    g[i].v = __half22float2(h);
+  });
+  if constexpr (L::D == 3) {  // (2D levels have no face buffer)
+    if (fw && fx) {
+      const long long F = (long long)v.n[1] * v.n[2];
+      const __half2* xb = reinterpret_cast<const __half2*>(xf) +
+                          ((long long)pair * 2 + (x != 0)) * L::Q * F + (long long)z * v.n[1] + y;
+      sfor<L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        g[i].v = __half22float2(xb[i * F]);
+      });
+    }
+  }
+  collide_emit_x2<L, COLL, MOV>(g, omega, R, [&](auto I, F2 val) {
+    constexpr int i = decltype(I)::value;
+    const __half2 h = __float22half2_rn(val.v);
+    if constexpr (PAR == 0)
+      f[opp<L>(i) * ph + a.at(0, 0, 0)] = h;
+    else
+      f[i * ph + a.at(L::c(i, 0), L::c(i, 1), L::c(i, 2))] = h;
+  });
 }
 
 // (drho, du, f^(1)) of a population set (deviations from the reference).
@@ -1282,15 +1253,21 @@ __device__ __forceinline__ bool node_of(const LevelView& v, long long t, int& x,
 // update (post-collision g_i at plane opp(i) of the node), in FP64 up to the
 // final rounding to the storage type.
 template <class L, class S>
-__global__ void k_init(LevelView v, int run, const double* rho, const double* u, RefState ref) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Nodes t0 .. t0 + cnt - 1 of the level (x fastest), from rho[t - t0] and
+// u[a * us + t - t0] (a chunk of the fields; us: the chunk's component
+// stride).
+__global__ void k_init(LevelView v, int run, const double* rho, const double* u, long long us,
+                       long long t0, long long cnt, RefState ref) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  const long long t = t0 + k;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
-  const long long N = (long long)v.n[0] * v.n[1] * v.n[2];
-  const double r = rho[t];
+  const double r = rho[k];
   double g0[L::Q];
-  equilibrium_dev<L, double>(r - ref.rho0, u[t] - ref.U[0], u[N + t] - ref.U[1],
-                             u[2 * N + t] - ref.U[2], ref.rho0, ref.U[0], ref.U[1], ref.U[2], g0);
+  equilibrium_dev<L, double>(r - ref.rho0, u[k] - ref.U[0], u[us + k] - ref.U[1],
+                             u[2 * us + k] - ref.U[2], ref.rho0, ref.U[0], ref.U[1], ref.U[2],
+                             g0);
   S* f = run_ptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   sfor<L::Q>([&](auto I) {
@@ -1358,15 +1335,18 @@ __global__ void __launch_bounds__(kDiagThreads)
 // rho and u (FP64 or FP32 outputs) of the post-collision state; NaN at
 // inactive nodes.
 template <class L, class S, class T>
-__global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, RefState ref) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// (nodes t0 .. t0 + cnt - 1 into rho[t - t0], u[a * us + t - t0])
+__global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, long long us,
+                         long long t0, long long cnt, RefState ref) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  const long long t = t0 + k;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
-  const long long N = (long long)v.n[0] * v.n[1] * v.n[2];
   if (inactive(v, x, y, z)) {
     const T nan = T(__longlong_as_double(0x7ff8000000000000ULL));
-    rho[t] = nan;
-    u[t] = u[N + t] = u[2 * N + t] = nan;
+    rho[k] = nan;
+    u[k] = u[us + k] = u[2 * us + k] = nan;
     return;
   }
   const S* f = run_cptr<S>(v, run);
@@ -1379,10 +1359,10 @@ __global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, RefState 
   for (int i = 0; i < L::Q; ++i) gd[i] = (double)g[i];
   moments<L, double>(gd, drho, jx, jy, jz);
   const double r = ref.rho0 + drho;
-  rho[t] = T(r);
-  u[t] = T((jx + ref.rho0 * ref.U[0]) / r);
-  u[N + t] = T((jy + ref.rho0 * ref.U[1]) / r);
-  u[2 * N + t] = T(L::D == 3 ? (jz + ref.rho0 * ref.U[2]) / r : 0.0);
+  rho[k] = T(r);
+  u[k] = T((jx + ref.rho0 * ref.U[0]) / r);
+  u[us + k] = T((jy + ref.rho0 * ref.U[1]) / r);
+  u[2 * us + k] = T(L::D == 3 ? (jz + ref.rho0 * ref.U[2]) / r : 0.0);
 }
 
 // Post-collision populations shifted by the rest state, f_i - w_i rho0,

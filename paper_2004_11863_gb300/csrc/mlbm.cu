@@ -84,6 +84,10 @@ struct Level {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Nodes per chunk of the host <-> device staging (lbm_init, lbm_macros):
+// two buffers of 4 doubles per node, 256 MB in all.
+constexpr long long kStageNodes = 1LL << 22;
+
 // Analytic initial fields (FP64) at the nodes of a level, the same
 // definitions as the host-side input generator: uniform flow; convected
 // vortex (Sec. 10.1, linearised density); Gaussian pulse (Sec. 9.2).
@@ -148,6 +152,7 @@ struct lbm_ctx {
   bool seeded = false;
   long long coarse_steps = 0;
   bool use_graphs = true;
+  bool use_xf = true;  // face buffers (lbm_set_face_buffer)
   // One graph per phase of a coarse step: level-0 parity (period 2) times
   // the history-slot rotation of every interface (period 3).
   static constexpr int kPhases = 6;
@@ -211,6 +216,32 @@ struct lbm_ctx {
       cudaFree(p);
   }
 
+  // Host <-> device staging of lbm_init and lbm_macros: fields move in
+  // chunks through two device buffers, copied on their own stream while the
+  // other buffer's chunk is converted on the handle's stream.
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_stage[2] = {}, ev_used[2] = {};
+  bool staging_ready() {
+    if (copy_stream) return true;
+    if (cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      copy_stream = nullptr;
+      return false;
+    }
+    for (int b = 0; b < 2; ++b)
+      if (cudaEventCreateWithFlags(&ev_stage[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_used[b], cudaEventDisableTiming) != cudaSuccess)
+        return false;
+    return true;
+  }
+  void staging_release() {
+    for (int b = 0; b < 2; ++b) {
+      if (ev_stage[b]) cudaEventDestroy(ev_stage[b]);
+      if (ev_used[b]) cudaEventDestroy(ev_used[b]);
+      ev_stage[b] = ev_used[b] = nullptr;
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
+  }
   // Device scratch of the synchronising set-up and read-out calls
   // (lbm_init, lbm_macros, lbm_populations): kept from one such call to the
   // next so that a loop over levels and runs allocates once; released when
@@ -273,6 +304,7 @@ void release(lbm_ctx* h) {
   h->dfree(h->probe_rec);
   h->dfree(h->probe_counter);
   h->scratch_drop();
+  h->staging_release();
   h->dfree(h->fused_tab);
   h->dfree(h->fused_prog);
   h->dfree(h->fused_start);
@@ -499,13 +531,14 @@ size_t hrr_sh_bytes(const lbm_ctx* h, int l) {
   return sizeof(float) * 3 * 6 * (size_t)h->lev[l].ring.K * h->batch;
 }
 
-// Device bytes of level l's face buffer (faces normal to a bounded x axis;
-// the hybrid collision, whose velocity pass reads the rebuilt nodes from the
-// planes, has none): two faces of n[1] n[2] nodes, q populations, every run
-// (binary16 run pairs: the batch rounded up to whole pairs).
+// Device bytes of level l's face buffer (3D levels, faces normal to a
+// bounded x axis; the hybrid collision, whose velocity pass reads the
+// rebuilt nodes from the planes, has none): two faces of n[1] n[2] nodes, q
+// populations, every run (binary16 run pairs: the batch rounded up to whole
+// pairs).
 size_t xf_bytes(const lbm_ctx* h, int l) {
   const Level& v = h->lev[l];
-  if (l < 1 || !v.boxed[0] || h->cfg.collision == LBM_HRR) return 0;
+  if (l < 1 || h->D != 3 || !v.boxed[0] || h->cfg.collision == LBM_HRR) return 0;
   const size_t es = v.view.es > 0 ? (size_t)v.view.es : 1;
   const size_t runs = (h->batch + es - 1) / es * es;
   const size_t s = h->cfg.storage == LBM_FP16_SHIFTED ? 2 : 4;
@@ -516,8 +549,9 @@ size_t xf_bytes(const lbm_ctx* h, int l) {
 // level's sensors are on (they read the rebuilt nodes from the planes).
 void* xf_of(const lbm_ctx* h, int l) {
   const Level& v = h->lev[l];
-  return v.sens_on ? nullptr : v.xf_mem;
+  return (v.sens_on || !h->use_xf) ? nullptr : v.xf_mem;
 }
+
 
 const float kTimeQuad[3] = {-1.0f / 8.0f, 3.0f / 4.0f, 3.0f / 8.0f};  // eq. TempInt
 const float kTimeLin[3] = {0.0f, 0.5f, 0.5f};   // first step: no t-1 yet
@@ -602,7 +636,8 @@ int advance(lbm_ctx* h, int l, const float* wt, bool launch, cudaEvent_t wait_be
     // streams above run the two side by side)
     if (h->recording)
       h->recording->push_back(Phase{3, l, par, 1 - c.last, {}, {}, resc, 0.0f, 1});
-    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref, h->cur));
+    LAUNCH_K(3, l, h->ops.restrict_tn(v.view, c.view, c.tn, st, resc, par, 1 - c.last, ref,
+                                      h->cur));
     if (fork) CK(cudaEventRecord(h->ev_restrict[l], h->side[l]));
     int rs = sensor_pass(h, l, par, launch, true);
     if (rs) return rs;
@@ -980,22 +1015,44 @@ int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* 
   }
   Level& v = h->lev[level];
   const long long N = v.n_nodes;
-  double* d = (double*)h->scratch_get(sizeof(double) * 4 * N);
+  // chunks of at most kStageNodes nodes through two staging buffers
+  const long long C = std::min(N, kStageNodes);
+  double* d = (double*)h->scratch_get(sizeof(double) * 4 * C * 2);
   if (!d) return LBM_ENOMEM;
+  if (!h->staging_ready()) return LBM_ECUDA;
   int rc = LBM_OK;
   do {
-    if (cudaMemcpyAsync(d, rho, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream) ||
-        cudaMemcpyAsync(d + N, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream)) {
-      rc = LBM_ECUDA;
+    cudaError_t e = cudaSuccess;
+    // the staging buffers' last users (an earlier set-up or read-out) are
+    // ordered on the handle's stream
+    if ((e = cudaEventRecord(h->ev_used[0], h->stream)) != cudaSuccess ||
+        (e = cudaEventRecord(h->ev_used[1], h->stream)) != cudaSuccess)
       break;
+    long long k = 0;
+    for (long long c0 = 0; c0 < N && e == cudaSuccess; c0 += C, ++k) {
+      const int b = (int)(k & 1);
+      const long long cnt = std::min(C, N - c0);
+      double* buf = d + (long long)b * 4 * C;
+      e = cudaStreamWaitEvent(h->copy_stream, h->ev_used[b], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf, rho + c0, sizeof(double) * cnt, cudaMemcpyHostToDevice,
+                            h->copy_stream);
+      for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+        e = cudaMemcpyAsync(buf + (1 + a) * C, u + a * N + c0, sizeof(double) * cnt,
+                            cudaMemcpyHostToDevice, h->copy_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_stage[b], h->copy_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_stage[b], 0);
+      if (e == cudaSuccess)
+        e = h->ops.init(v.view, h->cfg.storage, run, buf, buf + C, C, c0, cnt, h->ref,
+                        h->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_used[b], h->stream);
+      ++h->launches;
     }
-    cudaError_t e = h->ops.init(v.view, h->cfg.storage, run, d, d + N, h->ref, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
       snprintf(g_errmsg, sizeof(g_errmsg), "init: %s", cudaGetErrorString(e));
       rc = LBM_ECUDA;
     }
-    ++h->launches;
   } while (0);
   if (rc) return rc;
   h->inited[(size_t)level * h->batch + run] = 1;
@@ -1043,7 +1100,8 @@ int lbm_init_analytic(lbm_handle h, int run, const lbm_ic* ic) {
     k_ic_fields<<<(unsigned)((N + 127) / 128), 128, 0, h->stream>>>(v.view, pl, d, h->cfg.rho0,
                                                                     h->D, buf, buf + N);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = h->ops.init(v.view, h->cfg.storage, run, buf, buf + N, h->ref, h->stream);
+    if (e == cudaSuccess)
+      e = h->ops.init(v.view, h->cfg.storage, run, buf, buf + N, N, 0, N, h->ref, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     h->launches += 2;
     h->dfree(buf);
@@ -1333,15 +1391,38 @@ int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u) {
   if (!h->ready) return LBM_ESTATE;
   const Level& v = h->lev[level];
   const long long N = v.n_nodes;
-  double* d = (double*)h->scratch_get(sizeof(double) * 4 * N);
+  // chunks through two staging buffers: the read-out of one chunk (on the
+  // copy stream) overlaps the next chunk's moments (on the handle's stream)
+  const long long C = std::min(N, kStageNodes);
+  double* d = (double*)h->scratch_get(sizeof(double) * 4 * C * 2);
   if (!d) return LBM_ENOMEM;
-  cudaError_t e = h->ops.macros_d(v.view, h->cfg.storage, run, v.last, d, d + N, h->ref,
-                                  h->stream);
-  ++h->launches;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(rho, d, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(u, d + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream);
+  if (!h->staging_ready()) return LBM_ECUDA;
+  cudaError_t e = cudaSuccess;
+  long long k = 0;
+  for (long long c0 = 0; c0 < N && e == cudaSuccess; c0 += C, ++k) {
+    const int b = (int)(k & 1);
+    const long long cnt = std::min(C, N - c0);
+    double* buf = d + (long long)b * 4 * C;
+    // chunk k - 2's copies out of this buffer are done
+    if (k >= 2) e = cudaStreamWaitEvent(h->stream, h->ev_used[b], 0);
+    if (e == cudaSuccess)
+      e = h->ops.macros_d(v.view, h->cfg.storage, run, v.last, buf, buf + C, C, c0, cnt, h->ref,
+                          h->stream);
+    ++h->launches;
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_stage[b], h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->ev_stage[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rho + c0, buf, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
+                          h->copy_stream);
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+      e = cudaMemcpyAsync(u + a * N + c0, buf + (1 + a) * C, sizeof(double) * cnt,
+                          cudaMemcpyDeviceToHost, h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_used[b], h->copy_stream);
+  }
+  // the next user of the staging buffers runs on the handle's stream
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_used[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_used[1], 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     snprintf(g_errmsg, sizeof(g_errmsg), "macros: %s", cudaGetErrorString(e));
@@ -1361,6 +1442,14 @@ int lbm_set_block_shape(lbm_handle h, int level, int bx, int by) {
   CK(cudaStreamSynchronize(h->stream));
   v.k1_bx = bx;
   v.k1_by = by;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int lbm_set_face_buffer(lbm_handle h, int enable) {
+  if (!h || enable < 0 || enable > 1) return LBM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  h->use_xf = enable != 0;
   drop_graphs(h);
   return LBM_OK;
 }

@@ -53,10 +53,14 @@ struct Ops {
   cudaError_t (*sensor_read)(const LevelView& v, int run, const SensorState& st,
                              unsigned char* flags, double* div, double* curl, double* gnorm,
                              cudaStream_t s);
+  // (init, macros_d: nodes t0 .. t0 + cnt - 1 of the level, fields chunked
+  // as rho[t - t0], u[a * us + t - t0])
   cudaError_t (*init)(const LevelView& v, int storage, int run, const double* rho, const double* u,
-                      const RefState& ref, cudaStream_t s);
+                      long long us, long long t0, long long cnt, const RefState& ref,
+                      cudaStream_t s);
   cudaError_t (*macros_d)(const LevelView& v, int storage, int run, int last, double* rho,
-                          double* u, const RefState& ref, cudaStream_t s);
+                          double* u, long long us, long long t0, long long cnt,
+                          const RefState& ref, cudaStream_t s);
   cudaError_t (*macros_f)(const LevelView& v, int storage, int run, int last, float* rho, float* u,
                           const RefState& ref, cudaStream_t s);
   cudaError_t (*populations)(const LevelView& v, int storage, int run, int last, double* out,

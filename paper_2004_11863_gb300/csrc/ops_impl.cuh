@@ -378,34 +378,39 @@ inline long long nodes(const LevelView& v) { return (long long)v.n[0] * v.n[1] *
 
 template <class L>
 cudaError_t init(const LevelView& v, int storage, int run, const double* rho, const double* u,
-                 const RefState& ref, cudaStream_t s) {
-  unsigned g = blocks_for(nodes(v), 128);
+                 long long us, long long t0, long long cnt, const RefState& ref,
+                 cudaStream_t s) {
+  if (cnt <= 0) return cudaSuccess;
+  unsigned g = blocks_for(cnt, 128);
   if (storage == 0)
-    k_init<L, float><<<g, 128, 0, s>>>(v, run, rho, u, ref);
+    k_init<L, float><<<g, 128, 0, s>>>(v, run, rho, u, us, t0, cnt, ref);
   else
-    k_init<L, __half><<<g, 128, 0, s>>>(v, run, rho, u, ref);
+    k_init<L, __half><<<g, 128, 0, s>>>(v, run, rho, u, us, t0, cnt, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t macros_d(const LevelView& v, int storage, int run, int last, double* rho, double* u,
-                     const RefState& ref, cudaStream_t s) {
-  unsigned g = blocks_for(nodes(v), 128);
+                     long long us, long long t0, long long cnt, const RefState& ref,
+                     cudaStream_t s) {
+  if (cnt <= 0) return cudaSuccess;
+  unsigned g = blocks_for(cnt, 128);
   if (storage == 0)
-    k_macros<L, float, double><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
+    k_macros<L, float, double><<<g, 128, 0, s>>>(v, run, last, rho, u, us, t0, cnt, ref);
   else
-    k_macros<L, __half, double><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
+    k_macros<L, __half, double><<<g, 128, 0, s>>>(v, run, last, rho, u, us, t0, cnt, ref);
   return cudaGetLastError();
 }
 
 template <class L>
 cudaError_t macros_f(const LevelView& v, int storage, int run, int last, float* rho, float* u,
                      const RefState& ref, cudaStream_t s) {
-  unsigned g = blocks_for(nodes(v), 128);
+  const long long N = nodes(v);
+  unsigned g = blocks_for(N, 128);
   if (storage == 0)
-    k_macros<L, float, float><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
+    k_macros<L, float, float><<<g, 128, 0, s>>>(v, run, last, rho, u, N, 0, N, ref);
   else
-    k_macros<L, __half, float><<<g, 128, 0, s>>>(v, run, last, rho, u, ref);
+    k_macros<L, __half, float><<<g, 128, 0, s>>>(v, run, last, rho, u, N, 0, N, ref);
   return cudaGetLastError();
 }
 

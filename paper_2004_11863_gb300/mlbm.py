@@ -99,6 +99,7 @@ def lib():
     L.lbm_probe_async.argtypes = [P, dp, ctypes.c_int, ip]
     L.lbm_diag.argtypes = [P, ctypes.c_int, dp, dp]
     L.lbm_diag_noalloc.argtypes = [P, ctypes.c_int, dp, dp]
+    L.lbm_set_face_buffer.argtypes = [P, ctypes.c_int]
     L.lbm_bytes.argtypes = [ctypes.POINTER(lbm_config), ctypes.POINTER(ctypes.c_ulonglong)]
     L.lbm_init_analytic.argtypes = [P, ctypes.c_int, ctypes.POINTER(lbm_ic)]
     L.lbm_noise.argtypes = [P, P, ctypes.c_int, ctypes.c_int, dp, dp,
@@ -323,6 +324,11 @@ class Lbm:
 
     def set_block_shape(self, level, bx, by):
         _check(lib().lbm_set_block_shape(self._h, level, bx, by), "lbm_set_block_shape")
+
+    def set_face_buffer(self, enable: bool):
+        """lbm_set_face_buffer: route the rebuilt x-face nodes of 3D levels
+        through the face buffer (default) or through the population planes."""
+        _check(lib().lbm_set_face_buffer(self._h, int(bool(enable))), "lbm_set_face_buffer")
 
     def sensors_enable(self, level, eps=0.0, g_threshold=0.0):
         """lbm_sensors_enable: evaluate the non-hydrodynamic mode sensors of a

@@ -262,17 +262,19 @@ def pulse_2level_d2q9(collision: str = "RR", steps: int = 1500) -> Case:
                      amplitude=1e-3), steps)
 
 
-def vortex_slab_d3q19(steps: int = 500, side: int = 256) -> Case:
+def vortex_slab_d3q19(steps: int = 500, side: int = 256, yz: int = 0) -> Case:
     """Coarse side^3 D3Q19 (256^3), fine slab x in [side/2, side] (y, z
     periodic), RR, tau_c = 0.5 + 5e-5, vortex column about z, R = 8, at
     (side/2 - 28, side/2): (100, 128) at full size, so that the vortex centre
     reaches the interface after 500 steps at 0.1 c_s.  Smaller sides keep the
-    structure for bounded oracle runs."""
-    name = "vortex3d" if side == 256 else f"vortex3d_{side}"
-    return Case(name, "D3Q19", "RR", 0.5 + 5e-5, (side, side, side),
-                [((side // 2, 0, 0), (side, side, side))],
+    structure for bounded oracle runs; yz > 0 shrinks only the periodic y
+    and z extents (same rows as the full size, for profiling captures)."""
+    ny = yz or side
+    name = ("vortex3d" if side == 256 else f"vortex3d_{side}") + (f"_yz{yz}" if yz else "")
+    return Case(name, "D3Q19", "RR", 0.5 + 5e-5, (side, ny, ny),
+                [((side // 2, 0, 0), (side, ny, ny))],
                 dict(kind="vortex", u0=(0.1 * CS, 0.0, 0.0),
-                     center=(side / 2.0 - 28.0, side / 2.0),
+                     center=(side / 2.0 - 28.0, ny / 2.0),
                      radius=8.0, eps=0.05 * CS), steps)
 
 
