@@ -47,7 +47,17 @@ FALLBACK_HBM_GBS = 6800.0
 # (dram__bytes_read.sum + dram__bytes_write.sum), per active node of the
 # level and run, with the hash of the kernel sources it was taken on;
 # ignored once the sources change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the fine-
+    # level update of the same slab with full-width rows (257 fine nodes per
+    # row) and y, z cut to 128 fine nodes (vortex3d_yz64, a 2-run batch,
+    # 8,421,376 node updates per launch): odd launches 725.6 + 657.9 and
+    # 725.7 + 655.2 MB, even 723.9 + 599.1 and 723.9 + 599.2 MB; per node
+    # update 164.3, 164.0, 157.1 and 157.1 B, mean 160.6 B (152 B
+    # algorithmic).  The rows, and so the per-node traffic, are those of the
+    # full size.
+    ("vortex3d", "fp32", "update_L1"): {"bytes_per_node": 160.6, "src": "cc80c052ddf31322"},
+}
 
 
 def kernel_source_hash() -> str:

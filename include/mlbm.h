@@ -150,8 +150,11 @@ int lbm_level_info(lbm_handle h, int level, int* n, double* tau,
 /* Set every node of one level of one run to the equilibrium f^(0)(rho, u)
  * (eq. fEqH; initial populations carry no off-equilibrium part).
  * rho: host [N] doubles; u: host [3][N] doubles (u[2] ignored in 2D).
- * Synchronises on the handle's stream.  Its device buffer (4 N doubles) is
- * kept for the next lbm_init until every level of every run is set. */
+ * Synchronises on the handle's stream.  The fields are staged in chunks of
+ * 4 Mi nodes through two device buffers (at most 256 MB, shared with
+ * lbm_macros and kept until lbm_destroy), each chunk's host-to-device copy
+ * overlapping the conversion of the previous one; pinned host memory makes
+ * the copies run at full speed. */
 int lbm_init(lbm_handle h, int level, int run, const double* rho,
              const double* u);
 
@@ -209,9 +212,10 @@ int lbm_set_fused(lbm_handle h, int mode);
 
 /* Macroscopic density and velocity of one level of one run, from the
  * post-collision state after the last step: rho host [N], u host [3][N]
- * (u[2] = 0 in 2D); NaN at inactive nodes.  Synchronises.  The device
- * buffer it converts into (4 N doubles) is kept for further read-outs
- * (lbm_macros, lbm_populations) until the next lbm_step or lbm_destroy. */
+ * (u[2] = 0 in 2D); NaN at inactive nodes.  Synchronises.  Converted in
+ * chunks through lbm_init's two staging buffers, each chunk's device-to-host
+ * copy overlapping the conversion of the next; pinned host memory makes the
+ * copies run at full speed. */
 int lbm_macros(lbm_handle h, int level, int run, double* rho, double* u);
 
 /* Same as lbm_macros but into device buffers (float): rho_dev [N],

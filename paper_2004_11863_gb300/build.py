@@ -4,6 +4,10 @@ Each translation unit under csrc/ is compiled for sm_103a in parallel and
 linked into one shared library with a plain C ABI (include/mlbm.h).
 
     python -m paper_2004_11863_gb300.build [--force]
+
+MLBM_NVCC_EXTRA (environment, optional): extra nvcc flags appended to every
+compile, e.g. -D overrides of the tuning constants in kernels.cuh for a
+sweep; the library is rebuilt when they change.
 """
 from __future__ import annotations
 
@@ -44,15 +48,22 @@ def _nvcc():
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmlbm.so")
 
 
+def _extra():
+    return os.environ.get("MLBM_NVCC_EXTRA", "").split()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+    stamp = LIB + ".flags"
+    extra = _extra()
+    same = os.path.exists(stamp) and open(stamp).read() == " ".join(extra)
+    if not force and same and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
 
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -69,6 +80,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(" ".join(extra))
     return LIB
 
 

@@ -440,18 +440,32 @@ struct K1X2Tune<D3Q27> {
   static constexpr int MINB_H = K1X2H_MINB_D3Q27;
 };
 
+// z-planes per thread of the two-node update (1: one node pair per thread;
+// more: the thread walks that many consecutive planes and prefetches the
+// next plane's populations into L2 before colliding the current one, which
+// keeps DRAM reads in flight during the collision without holding
+// registers).  Binary32: 4 planes (+4 % on the D3Q19 slab, +3 % on the
+// nested D3Q27 case); binary16: 1 (its update is nearer the instruction
+// limit: the prefetches cost it 5-7 %).  Measured on GB300.
+#ifndef K1X2_PFZ_F
+#define K1X2_PFZ_F 4
+#endif
+#ifndef K1X2_PFZ_H
+#define K1X2_PFZ_H 1
+#endif
+template <class S>
+struct K1X2Pfz {
+  static constexpr int PZ = std::is_same<S, float>::value ? K1X2_PFZ_F : K1X2_PFZ_H;
+};
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <class L, class S, int COLL, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
-                                                                      : K1X2Tune<L>::MINB_H)
-    k_stream_collide_x2(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
-  int z = blockIdx.z, run = 0;
-  if (v.batch > 1) {
-    run = z / v.n[2];
-    z -= run * v.n[2];
-  }
-  if (x >= v.n[0]) return;
+__device__ __forceinline__ void stream_collide_x2_pair(const LevelView& v, float omega,
+                                                       const RefF& R, const S* __restrict__ xf,
+                                                       int x, int y0, int z, int run) {
   const bool ok0 = y0 < v.n[1] && !inactive(v, x, y0, z);
   const bool ok1 = y0 + 1 < v.n[1] && !inactive(v, x, y0 + 1, z);
   if (!ok0 && !ok1) return;
@@ -506,6 +520,49 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<
                      val.v.y);
     }
   });
+}
+
+template <class L, class S, int COLL, int PAR, bool MOV>
+__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
+                                                                      : K1X2Tune<L>::MINB_H)
+    k_stream_collide_x2(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
+  constexpr int PZ = K1X2Pfz<S>::PZ;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
+  const int nzb = (v.n[2] + PZ - 1) / PZ;  // z blocks per run
+  int zc = blockIdx.z, run = 0;
+  if (v.batch > 1) {
+    run = zc / nzb;
+    zc -= run * nzb;
+  }
+  if (x >= v.n[0]) return;
+  if constexpr (PZ == 1) {
+    stream_collide_x2_pair<L, S, COLL, PAR, MOV>(v, omega, R, xf, x, y0, zc, run);
+  } else {
+    const S* f = static_cast<const S*>(v.f) + run * v.run_stride;
+    const int ya = y0 < v.n[1] ? y0 : v.n[1] - 1, yb = y0 + 1 < v.n[1] ? y0 + 1 : ya;
+#pragma unroll 1
+    for (int k = 0; k < PZ; ++k) {
+      const int z = zc * PZ + k;
+      if (z >= v.n[2]) break;
+      if (k + 1 < PZ && z + 1 < v.n[2]) {  // the next plane's populations into L2
+        const NodeAddr p0 = node_addr<L>(v, x, ya, z + 1), p1 = node_addr<L>(v, x, yb, z + 1);
+        sfor<L::Q>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          if constexpr (PAR == 0) {
+            prefetch_l2(&f[(long long)i * v.plane + p0.at(0, 0, 0)]);
+            prefetch_l2(&f[(long long)i * v.plane + p1.at(0, 0, 0)]);
+          } else {
+            prefetch_l2(&f[(long long)opp<L>(i) * v.plane +
+                           p0.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
+            prefetch_l2(&f[(long long)opp<L>(i) * v.plane +
+                           p1.at(-L::c(i, 0), -L::c(i, 1), -L::c(i, 2))]);
+          }
+        });
+      }
+      stream_collide_x2_pair<L, S, COLL, PAR, MOV>(v, omega, R, xf, x, y0, z, run);
+    }
+  }
 }
 
 // Level update of binary16 storage with runs interleaved in pairs (es = 2):
@@ -1255,24 +1312,25 @@ __device__ __forceinline__ bool node_of(const LevelView& v, long long t, int& x,
 template <class L, class S>
 // Nodes t0 .. t0 + cnt - 1 of the level (x fastest), from rho[t - t0] and
 // u[a * us + t - t0] (a chunk of the fields; us: the chunk's component
-// stride).
+// stride).  The deviations from the reference state are formed in FP64 and
+// the equilibrium deviation in binary32, in the same deviation form as the
+// level update's collision (FP64 arithmetic is a small fraction of binary32
+// on this GPU; the stored populations are binary32 or binary16 either way).
 __global__ void k_init(LevelView v, int run, const double* rho, const double* u, long long us,
-                       long long t0, long long cnt, RefState ref) {
+                       long long t0, long long cnt, RefState ref, RefF R) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= cnt) return;
   const long long t = t0 + k;
   int x, y, z;
   if (!node_of(v, t, x, y, z)) return;
-  const double r = rho[k];
-  double g0[L::Q];
-  equilibrium_dev<L, double>(r - ref.rho0, u[k] - ref.U[0], u[us + k] - ref.U[1],
-                             u[2 * us + k] - ref.U[2], ref.rho0, ref.U[0], ref.U[1], ref.U[2],
-                             g0);
+  float g0[L::Q];
+  equilibrium_f<L>((float)(rho[k] - ref.rho0), (float)(u[k] - ref.U[0]),
+                   (float)(u[us + k] - ref.U[1]), (float)(u[2 * us + k] - ref.U[2]), R, g0);
   S* f = run_ptr<S>(v, run);
   const NodeAddr a = node_addr<L>(v, x, y, z);
   sfor<L::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    Store<S>::st(f + (long long)opp<L>(i) * v.plane + v.es * a.at(0, 0, 0), (float)g0[i]);
+    Store<S>::st(f + (long long)opp<L>(i) * v.plane + v.es * a.at(0, 0, 0), g0[i]);
   });
 }
 

@@ -243,10 +243,10 @@ struct lbm_ctx {
     copy_stream = nullptr;
   }
   // Device scratch of the synchronising set-up and read-out calls
-  // (lbm_init, lbm_macros, lbm_populations): kept from one such call to the
-  // next so that a loop over levels and runs allocates once; released when
-  // the last lbm_init completes the set-up, by the next lbm_step and by
-  // lbm_destroy.  Grows by
+  // (lbm_init, lbm_macros: the two staging buffers, at most 256 MB, kept
+  // until lbm_destroy so that set-up and read-out never allocate again;
+  // lbm_populations: one level's q FP64 planes, released after the call).
+  // Grows by
   // freeing before allocating, so it never holds more than the largest
   // single request.  Every user synchronises before returning, so the
   // buffer is idle whenever it is released.
@@ -923,6 +923,7 @@ int lbm_create(const lbm_config* cfg, void* stream, const lbm_allocator* alloc,
         return LBM_ENOMEM;
       }
       cudaMemsetAsync(v.xf_mem, 0, xb, h->stream);
+
     }
     const size_t db = hrr_du_bytes(h, l), sb = hrr_sh_bytes(h, l);
     if (db) {
@@ -1057,7 +1058,6 @@ int lbm_init(lbm_handle h, int level, int run, const double* rho, const double* 
   if (rc) return rc;
   h->inited[(size_t)level * h->batch + run] = 1;
   if (std::all_of(h->inited.begin(), h->inited.end(), [](char c) { return c != 0; })) {
-    h->scratch_drop();  // set-up done: hold no more than the run itself
     for (int l = 0; l < h->nlev; ++l) {
       h->lev[l].last = 0;
       h->lev[l].nsteps = 0;
@@ -1335,7 +1335,6 @@ int lbm_set_fused(lbm_handle h, int mode) {
 int lbm_step(lbm_handle h, int n_coarse) {
   if (!h || n_coarse < 0) return LBM_EINVAL;
   if (!h->ready) return LBM_ESTATE;
-  h->scratch_drop();
   if (!h->seeded) {
     int rc = seed_history(h);
     if (rc) return rc;
@@ -1603,6 +1602,7 @@ int lbm_populations(lbm_handle h, int level, int run, double* g) {
   ++h->launches;
   if (e == cudaSuccess) e = cudaMemcpyAsync(g, d, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->scratch_drop();  // (a level's q FP64 planes: not kept)
   if (e != cudaSuccess) {
     snprintf(g_errmsg, sizeof(g_errmsg), "populations: %s", cudaGetErrorString(e));
     return LBM_ECUDA;

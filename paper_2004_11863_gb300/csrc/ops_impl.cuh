@@ -38,7 +38,8 @@ cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefStat
                          int by, const S* xf, cudaStream_t s) {
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);
-  dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + 2 * by - 1) / (2 * by), v.n[2] * v.batch);
+  dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + 2 * by - 1) / (2 * by),
+            (v.n[2] + K1X2Pfz<S>::PZ - 1) / K1X2Pfz<S>::PZ * v.batch);
   const bool mov = ref.U[0] != 0.0 || ref.U[1] != 0.0 || ref.U[2] != 0.0;
   const RefF R = make_ref_f<L>(ref);
   if (mov) {
@@ -124,7 +125,8 @@ cudaError_t sc_coll(const LevelView& v, int coll, int par, float omega, const Re
 
 template <class L>
 cudaError_t stream_collide(const LevelView& v, int coll, int storage, int par, float omega,
-                           const RefState& ref, int bx, int by, const void* xf, cudaStream_t s) {
+                           const RefState& ref, int bx, int by, const void* xf,
+                           cudaStream_t s) {
   return storage == 0 ? sc_coll<L, float>(v, coll, par, omega, ref, bx, by, xf, s)
                       : sc_coll<L, __half>(v, coll, par, omega, ref, bx, by, xf, s);
 }
@@ -383,9 +385,10 @@ cudaError_t init(const LevelView& v, int storage, int run, const double* rho, co
   if (cnt <= 0) return cudaSuccess;
   unsigned g = blocks_for(cnt, 128);
   if (storage == 0)
-    k_init<L, float><<<g, 128, 0, s>>>(v, run, rho, u, us, t0, cnt, ref);
+    k_init<L, float><<<g, 128, 0, s>>>(v, run, rho, u, us, t0, cnt, ref, make_ref_f<L>(ref));
   else
-    k_init<L, __half><<<g, 128, 0, s>>>(v, run, rho, u, us, t0, cnt, ref);
+    k_init<L, __half><<<g, 128, 0, s>>>(v, run, rho, u, us, t0, cnt, ref,
+                                        make_ref_f<L>(ref));
   return cudaGetLastError();
 }
 

@@ -300,7 +300,7 @@ def check_face_buffer(case, batch=1, es=1):
                             assert e not in written
                             written[e] = (r, x, y, z, i)
         assert len(written) == batch * 2 * F * q
-        # the update: face warps and the slots each face lane reads
+        # the update: face warps and the face lanes (x = 0 and x = n[0] - 1)
         for bx in (32, 64, 128):
             nbx = -(-n[0] // bx)
             face_lanes = set()
