@@ -1334,6 +1334,47 @@ __global__ void k_init(LevelView v, int run, const double* rho, const double* u,
   });
 }
 
+// Moments of one node's binary32 populations for the read-out and the
+// diagnostics, as accurate as FP64 sums of the same values but formed with
+// binary32 instructions (GB300 executes FP64 at a small fraction of its
+// binary32 rate): each sum is accumulated in binary32 with the rounding
+// error of every addition recovered exactly by Knuth's TwoSum and summed
+// alongside (the cascaded summation Sum2 of Ogita, Rump and Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26, 2005); the pair is added in
+// FP64 at the end.  The result differs from the exact sum by at most
+// gamma_{n-1}^2 sum |g_i| (gamma_k = k u / (1 - k u), u = 2^-24, n <= 28
+// terms: below 1e-12 of sum |g_i|), plus the final FP64 rounding.
+struct Acc2 {
+  float s = 0.0f, e = 0.0f;
+  __device__ __forceinline__ void add(float b) {
+    const float x = s + b;  // TwoSum(s, b): x + err == s + b exactly
+    const float z = x - s;
+    e += (s - (x - z)) + (b - z);
+    s = x;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+
+// drho = sum g and j = sum xi g (shifted populations), each through Acc2.
+template <class L>
+__device__ __forceinline__ void moments_acc(const float (&g)[L::Q], double& drho, double& jx,
+                                            double& jy, double& jz) {
+  Acc2 r, m[3];
+  sfor<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    r.add(g[i]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (L::c(i, a) == 1) m[a].add(g[i]);
+      if (L::c(i, a) == -1) m[a].add(-g[i]);
+    }
+  });
+  drho = r.value();
+  jx = m[0].value();
+  jy = m[1].value();
+  jz = m[2].value();
+}
+
 // FP64 partials of the noise diagnostic: max |drho_a - drho_b| and the sum
 // of squares over level-0 nodes outside the child box by at least
 // `margin` cells (on every bounded axis the node lies outside the box
@@ -1362,12 +1403,13 @@ __global__ void __launch_bounds__(kDiagThreads)
       const S* fb = run_cptr<S>(vb, run);
       load_post<L, S>(fa, va.plane, node_addr<L>(va, x, y, z), last_a, va.es, ga);
       load_post<L, S>(fb, vb.plane, node_addr<L>(vb, x, y, z), last_b, vb.es, gb);
-      double da = 0.0, db = 0.0;
+      Acc2 sa, sb;  // (drho of both states to FP64 accuracy)
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
-        da += (double)ga[i];
-        db += (double)gb[i];
+        sa.add(ga[i]);
+        sb.add(gb[i]);
       }
+      const double da = sa.value(), db = sb.value();
       const double d = fabs((ra.rho0 + da) - (rb.rho0 + db));
       mx = d;
       ss = d * d;
@@ -1411,16 +1453,14 @@ __global__ void k_macros(LevelView v, int run, int last, T* rho, T* u, long long
   const NodeAddr a = node_addr<L>(v, x, y, z);
   float g[L::Q];
   load_post<L, S>(f, v.plane, a, last, v.es, g);
-  // moments summed in FP64 (read-out precision): rho u = sum xi g + rho0 U
-  double gd[L::Q], drho, jx, jy, jz;
-#pragma unroll
-  for (int i = 0; i < L::Q; ++i) gd[i] = (double)g[i];
-  moments<L, double>(gd, drho, jx, jy, jz);
-  const double r = ref.rho0 + drho;
+  // moments to FP64 accuracy (moments_acc): rho u = sum xi g + rho0 U
+  double drho, jx, jy, jz;
+  moments_acc<L>(g, drho, jx, jy, jz);
+  const double r = ref.rho0 + drho, ri = 1.0 / r;
   rho[k] = T(r);
-  u[k] = T((jx + ref.rho0 * ref.U[0]) / r);
-  u[us + k] = T((jy + ref.rho0 * ref.U[1]) / r);
-  u[2 * us + k] = T(L::D == 3 ? (jz + ref.rho0 * ref.U[2]) / r : 0.0);
+  u[k] = T((jx + ref.rho0 * ref.U[0]) * ri);
+  u[us + k] = T((jy + ref.rho0 * ref.U[1]) * ri);
+  u[2 * us + k] = T(L::D == 3 ? (jz + ref.rho0 * ref.U[2]) * ri : 0.0);
 }
 
 // Post-collision populations shifted by the rest state, f_i - w_i rho0,
@@ -1455,14 +1495,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(LevelView v, int 
     const NodeAddr a = node_addr<L>(v, x, y, z);
     float g[L::Q];
     load_post<L, S>(f, v.plane, a, last, v.es, g);
-    sfor<L::Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const double gi = (double)g[i];
-      s[0] += gi;
-      s[1] += L::c(i, 0) * gi;
-      s[2] += L::c(i, 1) * gi;
-      s[3] += L::c(i, 2) * gi;
-    });
+    moments_acc<L>(g, s[0], s[1], s[2], s[3]);
     for (int a = 0; a < 3; ++a) s[1 + a] += ref.rho0 * ref.U[a];
   }
 #pragma unroll
