@@ -416,6 +416,30 @@ __global__ void __launch_bounds__(128, MOV ? K1Tune<L, S>::MINB_MOV
 #ifndef K1X2_MINB_D3Q27
 #define K1X2_MINB_D3Q27 3
 #endif
+// MINB1: resident blocks of the binary32 odd-parity update, whose shifted
+// addresses need more registers: at the even update's bound it spilled
+// (D3Q19: 104 bytes at 128 registers); one block fewer holds it in
+// registers (D3Q19 168, D3Q27 252), +3 % on the D3Q19 slab's step and +2 %
+// on the nested D3Q27 case (GB300); both parities at the lower bound were
+// slower.
+#ifndef K1X2H_MINB1_D2Q9
+#define K1X2H_MINB1_D2Q9 K1X2H_MINB_D2Q9
+#endif
+#ifndef K1X2H_MINB1_D3Q19
+#define K1X2H_MINB1_D3Q19 K1X2H_MINB_D3Q19
+#endif
+#ifndef K1X2H_MINB1_D3Q27
+#define K1X2H_MINB1_D3Q27 K1X2H_MINB_D3Q27
+#endif
+#ifndef K1X2_MINB1_D2Q9
+#define K1X2_MINB1_D2Q9 K1X2_MINB_D2Q9
+#endif
+#ifndef K1X2_MINB1_D3Q19
+#define K1X2_MINB1_D3Q19 3
+#endif
+#ifndef K1X2_MINB1_D3Q27
+#define K1X2_MINB1_D3Q27 2
+#endif
 template <class L>
 struct K1X2Tune;
 template <>
@@ -423,21 +447,27 @@ struct K1X2Tune<D2Q9> {
   static constexpr bool ON = K1X2_D2Q9;
   static constexpr bool ON_H = K1X2H_D2Q9;
   static constexpr int MINB = K1X2_MINB_D2Q9;
+  static constexpr int MINB1 = K1X2_MINB1_D2Q9;
   static constexpr int MINB_H = K1X2H_MINB_D2Q9;
+  static constexpr int MINB1_H = K1X2H_MINB1_D2Q9;
 };
 template <>
 struct K1X2Tune<D3Q19> {
   static constexpr bool ON = K1X2_D3Q19;
   static constexpr bool ON_H = K1X2H_D3Q19;
   static constexpr int MINB = K1X2_MINB_D3Q19;
+  static constexpr int MINB1 = K1X2_MINB1_D3Q19;
   static constexpr int MINB_H = K1X2H_MINB_D3Q19;
+  static constexpr int MINB1_H = K1X2H_MINB1_D3Q19;
 };
 template <>
 struct K1X2Tune<D3Q27> {
   static constexpr bool ON = K1X2_D3Q27;
   static constexpr bool ON_H = K1X2H_D3Q27;
   static constexpr int MINB = K1X2_MINB_D3Q27;
+  static constexpr int MINB1 = K1X2_MINB1_D3Q27;
   static constexpr int MINB_H = K1X2H_MINB_D3Q27;
+  static constexpr int MINB1_H = K1X2H_MINB1_D3Q27;
 };
 
 // z-planes per thread of the two-node update (1: one node pair per thread;
@@ -523,8 +553,9 @@ __device__ __forceinline__ void stream_collide_x2_pair(const LevelView& v, float
 }
 
 template <class L, class S, int COLL, int PAR, bool MOV>
-__global__ void __launch_bounds__(128, std::is_same<S, float>::value ? K1X2Tune<L>::MINB
-                                                                      : K1X2Tune<L>::MINB_H)
+__global__ void __launch_bounds__(128, std::is_same<S, float>::value
+                                           ? (PAR ? K1X2Tune<L>::MINB1 : K1X2Tune<L>::MINB)
+                                           : (PAR ? K1X2Tune<L>::MINB1_H : K1X2Tune<L>::MINB_H))
     k_stream_collide_x2(LevelView v, float omega, RefF R, const S* __restrict__ xf) {
   constexpr int PZ = K1X2Pfz<S>::PZ;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;

@@ -381,13 +381,17 @@ int build_layout(lbm_ctx* h) {
   return LBM_OK;
 }
 
-// Storage geometry (ghost skin on bounded axes, 32-element row pitch).
+// Storage geometry (ghost skin on bounded axes, row pitch a multiple of
+// MLBM_ROW_ALIGN elements).
+#ifndef MLBM_ROW_ALIGN
+#define MLBM_ROW_ALIGN 32
+#endif
 void build_view(lbm_ctx* h, int l) {
   Level& v = h->lev[l];
   LevelView& w = v.view;
   int g[3];
   for (int a = 0; a < 3; ++a) g[a] = v.per[a] ? 0 : 1;
-  w.SX = round_up(v.n[0] + 2 * g[0], 32);
+  w.SX = round_up(v.n[0] + 2 * g[0], MLBM_ROW_ALIGN);
   w.SY = v.n[1] + 2 * g[1];
   const long long SZ = v.n[2] + 2 * g[2];
   w.off = 32 + ((long long)g[2] * w.SY + g[1]) * w.SX;
