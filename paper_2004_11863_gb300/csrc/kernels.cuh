@@ -576,7 +576,10 @@ __global__ void __launch_bounds__(128, std::is_same<S, float>::value
     for (int k = 0; k < PZ; ++k) {
       const int z = zc * PZ + k;
       if (z >= v.n[2]) break;
-      if (k + 1 < PZ && z + 1 < v.n[2]) {  // the next plane's populations into L2
+      // the next plane's populations into L2 (not for nodes a parent level
+      // leaves to its child: they are not updated)
+      if (k + 1 < PZ && z + 1 < v.n[2] &&
+          !(inactive(v, x, ya, z + 1) && inactive(v, x, yb, z + 1))) {
         const NodeAddr p0 = node_addr<L>(v, x, ya, z + 1), p1 = node_addr<L>(v, x, yb, z + 1);
         sfor<L::Q>([&](auto I) {
           constexpr int i = decltype(I)::value;
