@@ -335,3 +335,4 @@ def test_face_buffer_test_layouts(name, case):
                          ids=["vortex3d_64", "pulse3d_48"])
 def test_face_buffer_benchmark_layouts(name, mk):
     check_face_buffer(mk(), batch=1, es=1)
+
