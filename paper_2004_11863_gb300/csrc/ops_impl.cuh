@@ -37,6 +37,7 @@ template <class L, class S, int COLL>
 cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx,
                          int by, const S* xf, cudaStream_t s) {
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
+  if (v.run_stride >= (1LL << 31)) return cudaErrorInvalidValue;  // (32-bit offsets)
   dim3 block(bx, by, 1);
   dim3 grid((v.n[0] + bx - 1) / bx, (v.n[1] + 2 * by - 1) / (2 * by),
             (v.n[2] + K1X2Pfz<S>::PZ - 1) / K1X2Pfz<S>::PZ * v.batch);
@@ -59,9 +60,11 @@ cudaError_t sc_x2_launch(const LevelView& v, int par, float omega, const RefStat
 template <class L, class S, int COLL>
 cudaError_t sc_launch(const LevelView& v, int par, float omega, const RefState& ref, int bx, int by,
                       const S* xf, cudaStream_t s) {
+  // (the two-node update addresses a run with 32-bit offsets: larger runs
+  // take the one-node update)
   if constexpr ((std::is_same<S, float>::value && K1X2Tune<L>::ON) ||
                 (std::is_same<S, __half>::value && K1X2Tune<L>::ON_H))
-    return sc_x2_launch<L, S, COLL>(v, par, omega, ref, bx, by, xf, s);
+    if (v.run_stride < (1LL << 31)) return sc_x2_launch<L, S, COLL>(v, par, omega, ref, bx, by, xf, s);
   constexpr int NPT = K1Tune<L, S>::NPT;
   if (bx < 32 || bx % 32 != 0 || by < 1 || bx * by > 128) return cudaErrorInvalidValue;
   dim3 block(bx, by, 1);
