@@ -188,6 +188,7 @@ struct FusedArgs {
   int* err_host;              // mapped host memory: the error word after the launch
   long long spin_limit;       // bounded waits
   int expect_extra;           // barrier expects this many blocks beyond the grid (0; tests > 0)
+  int cluster;                // 1: the grid is one thread-block cluster (hardware barrier)
 };
 
 struct FusedHost {

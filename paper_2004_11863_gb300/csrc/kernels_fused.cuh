@@ -34,6 +34,10 @@
 // limit); a wait that runs out sets the error word, every block then leaves
 // the program, and the host reads the error word (mapped host memory)
 // after the launch.  The launch is cooperative, so all blocks are resident.
+// A run small enough for one thread-block cluster (at most 16 blocks, a few
+// items per thread) is launched as one cluster instead and takes the
+// cluster's hardware barrier (cluster_barrier), a fraction of the cost of
+// the global one.
 #pragma once
 #include "kernels.cuh"
 
@@ -88,6 +92,23 @@ __device__ __forceinline__ bool fused_barrier(const FusedArgs& A) {
   }
   __syncthreads();
   return *(volatile int*)A.err == 0;
+}
+
+// The barrier of a grid that is one thread-block cluster: the cluster's
+// hardware barrier, with release / acquire ordering at cluster scope (the
+// blocks' global-memory writes before it are visible to every block after
+// it).  Every block takes every barrier of the program (the phase loop is
+// the same for all blocks and none leaves it early), so it cannot wait on
+// a block that never arrives; the bounded software barrier serves the
+// timeout test.
+__device__ __forceinline__ bool cluster_barrier() {
+  __threadfence();
+  __syncthreads();
+  asm volatile(
+      "barrier.cluster.arrive.release;\n\t"
+      "barrier.cluster.wait.acquire;" ::
+          : "memory");
+  return true;
 }
 
 // Level update of node item t (run-major over the level's nodes).
@@ -354,7 +375,7 @@ __global__ void __launch_bounds__(kFusedThreads, FUSED_MINB) k_fused(const __gri
           if (blockIdx.x == 0) fused_probe<L, S>(T, T.v[l], ph.par);
           break;
       }
-      if (!ph.nobar) ok = fused_barrier(A);
+      if (!ph.nobar) ok = A.cluster ? cluster_barrier() : fused_barrier(A);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -191,6 +191,7 @@ struct lbm_ctx {
   int* fused_err_host = nullptr;      // mapped pinned host memory
   int* fused_err_dev = nullptr;       // its device alias
   int fused_blocks = 0;
+  bool fused_cluster = false;  // the fused grid is one cluster
   // probes
   int probe_level = -1, probe_n = 0, probe_cap = 0;
   long long probe_pending = 0;  // coarse steps recorded since the last read-out
@@ -1265,7 +1266,17 @@ int fused_prepare(lbm_ctx* h) {
     snprintf(g_errmsg, sizeof(g_errmsg), "fused step: no co-resident grid");
     return LBM_ECUDA;
   }
-  h->fused_blocks = (int)std::min<long long>(maxb, (items + 255) / 256);
+  const long long need = (items + 255) / 256;
+  h->fused_blocks = (int)std::min<long long>(maxb, need);
+  // a run that fits one cluster at four items a thread or fewer runs as one
+  // cluster with the hardware barrier (not the timeout test's mode 2: its
+  // barrier must be the bounded one)
+  h->fused_cluster = false;
+  const int maxc = h->fused == 1 ? h->ops.fused_max_cluster(h->cfg.storage) : 0;
+  if (maxc >= 2 && need <= 4LL * maxc) {
+    h->fused_blocks = (int)std::min<long long>(maxc, need);
+    h->fused_cluster = h->fused_blocks >= 2;
+  }
   h->fused_valid = true;
   return LBM_OK;
 }
@@ -1296,6 +1307,7 @@ int fused_steps(lbm_ctx* h, int n) {
     // read latency of every probe; the barrier test needs milliseconds
     A.spin_limit = h->fused == 2 ? (1LL << 12) : (1LL << 21);
     A.expect_extra = h->fused == 2 ? 1 : 0;
+    A.cluster = h->fused_cluster ? 1 : 0;
     CK(h->ops.fused(A, h->cfg.storage, h->fused_blocks, h->stream));
     ++h->launches;
     for (int s = 0; s < chunk; ++s) {

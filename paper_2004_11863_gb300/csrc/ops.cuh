@@ -76,10 +76,12 @@ struct Ops {
                        cudaStream_t s);
   // Persistent fused step (kernels_fused.cuh): bytes of the device tables;
   // fill them from the host description (synchronous copy); the largest
-  // co-resident grid; one cooperative launch of `blocks` blocks.
+  // co-resident grid; the largest cluster; one launch of `blocks` blocks
+  // (cooperative, or one cluster when A.cluster).
   size_t (*fused_tab_bytes)();
   cudaError_t (*fused_setup)(const FusedHost& hst, void* d_tab);
   int (*fused_max_blocks)(int storage);
+  int (*fused_max_cluster)(int storage);
   cudaError_t (*fused)(const FusedArgs& A, int storage, int blocks, cudaStream_t s);
 };
 
@@ -90,6 +92,8 @@ template <class L>
 cudaError_t fused_setup(const FusedHost& hst, void* d_tab);
 template <class L>
 int fused_max_blocks(int storage);
+template <class L>
+int fused_max_cluster(int storage);
 template <class L>
 cudaError_t fused_launch(const FusedArgs& A, int storage, int blocks, cudaStream_t s);
 

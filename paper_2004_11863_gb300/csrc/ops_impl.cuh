@@ -492,6 +492,7 @@ Ops make_ops() {
   o.fused_tab_bytes = fused_tab_bytes<L>;
   o.fused_setup = fused_setup<L>;
   o.fused_max_blocks = fused_max_blocks<L>;
+  o.fused_max_cluster = fused_max_cluster<L>;
   o.fused = fused_launch<L>;
   return o;
 }
