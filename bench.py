@@ -51,12 +51,12 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the fine-
     # level update of the same slab with full-width rows (257 fine nodes per
     # row) and y, z cut to 128 fine nodes (vortex3d_yz64, a 2-run batch,
-    # 8,421,376 node updates per launch): odd launches 722.3 + 603.7 and
-    # 722.4 + 601.5 MB, even 724.0 + 599.2 and 723.9 + 599.1 MB; per node
-    # update 157.5, 157.2, 157.1 and 157.1 B, mean 157.2 B (152 B
+    # 8,421,376 node updates per launch): odd launches 722.5 + 604.9 and
+    # 722.6 + 601.7 MB, even 727.4 + 599.9 and 727.3 + 599.7 MB; per node
+    # update 157.6, 157.3, 157.6 and 157.6 B, mean 157.5 B (152 B
     # algorithmic).  The rows, and so the per-node traffic, are those of the
     # full size.
-    ("vortex3d", "fp32", "update_L1"): {"bytes_per_node": 157.2, "src": "7a368e6950b9ccde"},
+    ("vortex3d", "fp32", "update_L1"): {"bytes_per_node": 157.5, "src": "c278bde650f8157f"},
 }
 
 

@@ -474,11 +474,12 @@ struct K1X2Tune<D3Q27> {
 // more: the thread walks that many consecutive planes and prefetches the
 // next plane's populations into L2 before colliding the current one, which
 // keeps DRAM reads in flight during the collision without holding
-// registers).  Binary32: 4 planes (+4 % on the D3Q19 slab, +3 % on the
-// nested D3Q27 case); binary16: 1 (its update is nearer the instruction
+// registers).  Binary32: 8 planes (against one: +9 % on the D3Q19 slab;
+// against four: +1.3 % there and +1 % on the nested D3Q27 case; sixteen
+// measured no better); binary16: 1 (its update is nearer the instruction
 // limit: the prefetches cost it 5-7 %).  Measured on GB300.
 #ifndef K1X2_PFZ_F
-#define K1X2_PFZ_F 4
+#define K1X2_PFZ_F 8
 #endif
 #ifndef K1X2_PFZ_H
 #define K1X2_PFZ_H 1
