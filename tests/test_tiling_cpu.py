@@ -336,3 +336,62 @@ def test_face_buffer_test_layouts(name, case):
 def test_face_buffer_benchmark_layouts(name, mk):
     check_face_buffer(mk(), batch=1, es=1)
 
+
+
+def pz_planes(storage):
+    """z-planes each thread of the two-node update walks (K1X2_PFZ_F / _H)."""
+    s = _src()
+    f = int(re.search(r"#define K1X2_PFZ_F (\d+)", s).group(1))
+    h = int(re.search(r"#define K1X2_PFZ_H (\d+)", s).group(1))
+    return f if storage == "fp32" else h
+
+
+def check_x2_walk(n, batch, bx, by, pz):
+    """Replays k_stream_collide_x2's block / thread / z-walk mapping: every
+    node of every run is updated exactly once, by a thread whose walk stays
+    inside the level and whose prefetch targets the plane it walks to next."""
+    nbx, nby, nzb = -(-n[0] // bx), -(-n[1] // (2 * by)), -(-n[2] // pz)
+    seen = {}
+    for bz in range(nzb * batch):
+        run, zc = (bz // nzb, bz % nzb) if batch > 1 else (0, bz)
+        for byi in range(nby):
+            for ty in range(by):
+                y0 = (byi * by + ty) * 2
+                for k in range(pz):
+                    z = zc * pz + k
+                    if z >= n[2]:
+                        break
+                    if k + 1 < pz and z + 1 < n[2]:
+                        assert zc * pz + k + 1 == z + 1 < n[2]
+                    for yy in (y0, y0 + 1):
+                        if yy >= n[1]:
+                            continue
+                        key = (run, z, yy)
+                        seen[key] = seen.get(key, 0) + 1
+    # x: every node of a row by exactly one lane of the row's x blocks
+    lanes = [b * bx + t for b in range(nbx) for t in range(bx) if b * bx + t < n[0]]
+    assert lanes == list(range(n[0]))
+    assert len(seen) == batch * n[1] * n[2] and set(seen.values()) == {1}
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_x2_walk_covers_every_node_once(storage):
+    """For the test and benchmark 3D layouts' levels, every block shape the
+    autotuner tries, one and three runs."""
+    pz = pz_planes(storage)
+    cases = [c for _, c in LAYOUTS] + [mk() for _, mk in BENCH]
+    shapes = [(32, 4), (32, 2), (32, 1), (64, 2), (64, 1), (128, 1), (32, 3)]
+    done = 0
+    for case in cases:
+        D, L = levels(case)
+        if D != 3:
+            continue
+        for lev in L:
+            n = lev["n"]
+            if n[0] * n[1] * n[2] > 3_000_000:
+                n = [n[0], min(n[1], 70), min(n[2], 37)]  # (the mapping does not depend on size)
+            for bx, by in shapes:
+                for batch in (1, 3):
+                    check_x2_walk(n, batch, bx, by, pz)
+                    done += 1
+    assert done > 0
